@@ -1,0 +1,175 @@
+/*
+ * rsnegf.h -- C ABI of the GB300 (sm_103a) real-space NEGF transmission library.
+ *
+ * The library computes, on one GPU, the Landauer transmission of a junction
+ * described on a real-space grid with absorbing boundary conditions
+ * (Feldman, Seideman, Hod & Kronik, "A real-space method for highly
+ * parallelizable electronic transport calculations"):
+ *
+ *   H_op   = H_KS - i Gamma,  Gamma = Gamma_L + Gamma_R          (Sec. II.B, Eq. Hop)
+ *   G^r(E) = (E 1 - H_op)^{-1} = (E - H_KS + i Gamma)^{-1}        (Sec. II.A, Eq. G)
+ *   T(E)   = 4 sum_{i in L, j in R} Gamma_L,i Gamma_R,j |G_ij|^2  (Sec. II.B, Eq. T-realspace;
+ *            the factor 4 is the coupling Gamma_std = 2*CAP, since the CAP is the
+ *            anti-Hermitian part of the lead self-energy)
+ *
+ * H_KS is real symmetric: -1/2 times an order-2R finite-difference Laplacian,
+ * a local potential V_loc and separable Kleinman-Bylander projectors
+ * (Sec. II.C: the only off-diagonal entries are the FD stencil and the
+ * cutoff-limited nonlocal part).  Because H_op is complex symmetric
+ * (Eq. complex-sym) G = G^T, so T needs only the columns x_j = G e_j for the
+ * grid points j with Gamma_R,j > 0.  Each column is found by a Krylov solve of
+ * A(E) x_j = e_j (conjugate orthogonal conjugate gradients, COCG -- the paper
+ * itself diagonalises instead; the column solve is this library's route),
+ * with iterative refinement on the true residual in FP64.
+ *
+ * Conventions for every entry point:
+ *  - Grid: nx*ny*nz points, flat index ix + nx*(iy + ny*iz) (x fastest),
+ *    spacing h (bohr), zero (Dirichlet) values outside the box on every axis.
+ *    Transport axis z.  Energies in hartree.
+ *  - Complex vectors are interleaved (re, im): complex128 = two doubles,
+ *    complex64 = two floats.
+ *  - Pointers named *_dev are device pointers (cudaMalloc / PyTorch memory on
+ *    the context's device); every other pointer is host memory.  The caller owns
+ *    all buffers it passes; setters copy their inputs, so host arrays may be
+ *    freed after the call returns.
+ *  - Work is queued on the context's stream.  Calls that return host results
+ *    (T, dV, iteration counts) synchronise that stream before returning; calls
+ *    that only write *_dev buffers may return before the GPU is done.
+ *  - Every call returns an rsn_status and never aborts the process; on failure
+ *    rsn_last_error() describes the cause.  A context is used by one host
+ *    thread at a time.
+ */
+#ifndef RSNEGF_H
+#define RSNEGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsn_ctx rsn_ctx; /* opaque: device copies of the setup data, workspaces, graphs */
+
+typedef enum {
+    RSN_OK = 0,
+    RSN_EINVAL = -1,     /* bad argument (null pointer, size, range, call order) */
+    RSN_ENOMEM = -2,     /* device or host allocation failed */
+    RSN_ECUDA = -3,      /* a CUDA runtime call failed (no device, launch error, ...) */
+    RSN_ENOCONV = -4,    /* some columns missed the tolerance within max_outer sweeps */
+    RSN_ETIMEOUT = -5,   /* deadline_ms elapsed before every column converged */
+    RSN_EBREAKDOWN = -6, /* COCG breakdown (p^T A p ~ 0) persisted across restarts */
+    RSN_ESTATE = -7      /* required setter not called yet */
+} rsn_status;
+
+enum { RSN_FP64 = 0, RSN_MIXED = 1 };
+
+/* Solver options (rsn_default_opts fills every field). */
+typedef struct {
+    int precision;      /* RSN_FP64: complex FP64 Krylov recurrence;
+                           RSN_MIXED: complex FP32 recurrence on the correction
+                           equation, FP64 true residual / update / T sums. */
+    double tol;         /* stop when ||b - A x||_2 <= tol * ||b||_2 (true residual, FP64) */
+    double tol_inner;   /* each refinement sweep reduces its recurrence residual by this factor */
+    int max_iter;       /* cap on Krylov iterations per refinement sweep */
+    int max_outer;      /* cap on refinement sweeps */
+    double deadline_ms; /* wall-clock budget of the call, 0 = none */
+    int rhs_block;      /* systems solved concurrently (0 = choose from free memory) */
+    int use_graph;      /* 1: replay the iteration body as a captured CUDA graph */
+    int graph_iters;    /* iterations per graph replay between convergence polls */
+} rsn_solver_opts;
+
+/* Defaults for a precision: FP64 -> tol 1e-13, tol_inner 1e-11;
+   MIXED -> tol 1e-10, tol_inner 1e-5; max_iter 4000, max_outer 8, graphs on. */
+void rsn_default_opts(int precision, rsn_solver_opts* opts);
+
+/* Create a context on CUDA device `device`, queuing work on `cuda_stream`
+   (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+   context.  Errors: RSN_EINVAL (out NULL), RSN_ECUDA (no such device). */
+rsn_status rsn_create(rsn_ctx** out, int device, void* cuda_stream);
+
+/* Free every device and host resource of the context (NULL is a no-op). */
+rsn_status rsn_destroy(rsn_ctx* ctx);
+
+/* Grid and FD order (Sec. II.C: high-order FD Laplacian).  fd_half_order R in
+   1..6 selects the order-2R central stencil (R = 1: 7-point, R = 4: 25-point,
+   R = 6: 37-point).  Invalidates every other setter's data.
+   Errors: RSN_EINVAL (sizes < 1, nx*ny > 4096, R out of range, h <= 0). */
+rsn_status rsn_set_grid(rsn_ctx* ctx, int nx, int ny, int nz, double h, int fd_half_order);
+
+/* Local potential V_loc (hartree), N = nx*ny*nz doubles, host memory.
+   Errors: RSN_ESTATE (no grid), RSN_EINVAL (NULL). */
+rsn_status rsn_set_potential(rsn_ctx* ctx, const double* v_loc);
+
+/* Kleinman-Bylander projectors in compressed rows (Sec. II.C, nonlocal
+   pseudopotential with a cutoff radius):  H_nl = sum_p e_kb[p] v_p v_p^T,
+   v_p[idx[k]] = val[k] for k in offsets[p] .. offsets[p+1]-1.
+   The values carry the quadrature weight (val = beta * sqrt(h^3)).  Consecutive
+   projectors with identical index lists are treated as one atom (one gather).
+   n_proj = 0 removes all projectors.  Host arrays.
+   Errors: RSN_ESTATE (no grid), RSN_EINVAL (index out of range, offsets not
+   non-decreasing, n_proj > 65536). */
+rsn_status rsn_set_projectors(rsn_ctx* ctx, int n_proj, const int64_t* offsets,
+                              const int32_t* idx, const double* val, const double* e_kb);
+
+/* Absorbing potentials Gamma_L, Gamma_R >= 0 (hartree), N doubles each, host
+   (Sec. II.B, Eqs. Hop and ABC).  They enter A(E) as +i(Gamma_L + Gamma_R) and
+   act as the lead couplings in T.  Errors: RSN_ESTATE, RSN_EINVAL (negative). */
+rsn_status rsn_set_cap(rsn_ctx* ctx, const double* gamma_l, const double* gamma_r);
+
+/* y_k = A(E_k) x_k for n_rhs vectors (the matvec of Eqs. G/Hop: FD stencil,
+   V_loc, CAP and projectors).  x_dev, y_dev: device, [n_rhs][N] complex128
+   (precision RSN_FP64) or complex64 (RSN_MIXED).  E: host, n_rhs doubles.
+   Errors: RSN_ESTATE, RSN_EINVAL, RSN_ECUDA. */
+rsn_status rsn_apply(rsn_ctx* ctx, int precision, int n_rhs, const double* E,
+                     const void* x_dev, void* y_dev);
+
+/* Green's-function columns x_{e,c} = G^r(E[e]) e_{cols[c]} (Eq. G).
+   x_dev: device, [n_e][n_cols][N] complex128, written in place.  iters / relres
+   (host, n_e*n_cols each, may be NULL) receive the total Krylov iterations and
+   the final true relative residual; a column that did not converge gets
+   iters < 0.  Errors: RSN_ESTATE, RSN_EINVAL (cols out of range), RSN_ENOMEM,
+   RSN_ENOCONV / RSN_ETIMEOUT / RSN_EBREAKDOWN (x_dev still holds the best iterate). */
+rsn_status rsn_solve_columns(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                             const int32_t* cols, const rsn_solver_opts* opts,
+                             void* x_dev, int32_t* iters, double* relres);
+
+/* T(E) by Eq. T-realspace restricted to the given columns:
+   T[e] = 4 sum_c Gamma_R[cols[c]] sum_{i: Gamma_L,i > 0} Gamma_L,i |G_{i,cols[c]}(E[e])|^2.
+   With cols = every point where Gamma_R > 0 this is the full transmission.
+   T: host, n_e doubles.  Sums run in FP64 in a fixed order (bit-reproducible).
+   Errors: as rsn_solve_columns (T still filled from the best iterates). */
+rsn_status rsn_transmission(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                            const int32_t* cols, const rsn_solver_opts* opts, double* T);
+
+/* Vector-Jacobian product of T with respect to V_loc:
+   dV[r] = sum_e T_bar[e] dT(E[e])/dV_loc(r)
+         = sum_e T_bar[e] 8 sum_c Gamma_R,c Re(lambda_{e,c}(r) x_{e,c}(r)),
+   lambda = G (Gamma_L o conj(x)) -- one adjoint solve per column with the same
+   operator, since G^T = G (Eq. complex-sym).  T_bar: host, n_e doubles.
+   dV: host or device (dV_is_device) N doubles, overwritten.  T: host n_e
+   doubles or NULL (receives T(E) of the forward pass).  Errors: as above. */
+rsn_status rsn_transmission_vjp(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                                const int32_t* cols, const rsn_solver_opts* opts,
+                                const double* T_bar, double* dV, int dV_is_device,
+                                double* T);
+
+/* Counters of the last solve on this context: total Krylov iterations over all
+   columns, refinement sweeps, device kernel launches queued, and elapsed GPU
+   milliseconds of the solve phase.  Any pointer may be NULL. */
+rsn_status rsn_last_stats(const rsn_ctx* ctx, int64_t* krylov_iters, int64_t* sweeps,
+                          int64_t* launches, double* gpu_ms);
+
+/* Override the operator kernel's tile (0 = automatic): TY rows of the x-y
+   plane per CTA, Lz planes per CTA along z, ppt owned points per thread
+   (1..4).  Used by the autotuner and by tests that force ragged tiles; it does
+   not change results beyond rounding order.  Errors: RSN_EINVAL. */
+rsn_status rsn_set_tiling(rsn_ctx* ctx, int TY, int Lz, int ppt);
+
+/* Human-readable description of the context's last error ("" if none).
+   ctx may be NULL (reports errors from rsn_create). */
+const char* rsn_last_error(const rsn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSNEGF_H */

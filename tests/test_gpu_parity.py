@@ -1,0 +1,143 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances: FP64 mode -- columns ||dx||/||x|| <= 1e-9 and |dT| <= 1e-9 max(|T|, 1e-3);
+mixed mode (FP32 Krylov + FP64 refinement to relative residual 1e-10) --
+|dT| <= 1e-6 absolute.  The operator itself is checked element-wise:
+FP64 to 1e-12 relative (rounding order only), FP32 to 2e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1401_0782_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_0782_gb300 import binding
+    return binding
+
+
+def _rand_x(rng, n, N, dtype):
+    x = rng.standard_normal((n, N)) + 1j * rng.standard_normal((n, N))
+    return torch.tensor(x, dtype=dtype, device="cuda")
+
+
+JUNCTIONS = {
+    "waveguide_R1": lambda: P.waveguide(nx=8, ny=8, nz=48),
+    "junction_R4": lambda: P.molecular_junction(seed=3, nx=12, ny=12, nz=40, n_wells=4, n_cap=5),
+    "ragged_R3": lambda: P.molecular_junction(seed=5, nx=13, ny=11, nz=37, fd_half_order=3, n_wells=3, n_cap=4),
+    "spd_R6": lambda: P.molecular_junction(seed=4, nx=12, ny=12, nz=40, fd_half_order=6, n_wells=3, lmax=2,
+                                           n_cap=6, h=0.3),
+    "wide_R2": lambda: P.molecular_junction(seed=6, nx=40, ny=36, nz=20, fd_half_order=2, n_wells=2, n_cap=3),
+}
+
+
+@pytest.mark.parametrize("name", sorted(JUNCTIONS))
+@pytest.mark.parametrize("tiling", [(0, 0, 0), (5, 7, 2), (3, 9, 1)])
+def test_apply_matches_oracle_operator(B, name, tiling):
+    j = JUNCTIONS[name]()
+    ctx = B.Context(0).set_junction(j)
+    ctx.set_tiling(*tiling)
+    rng = np.random.default_rng(1)
+    E = np.array([0.2, -0.7, 1.3])
+    x64 = _rand_x(rng, E.size, j.N, torch.complex128)
+    y64 = ctx.apply(E, x64, B.RSN_FP64).cpu().numpy()
+    xh = x64.cpu().numpy()
+    ref = np.stack([O.apply_operator(j, e, xh[k]) for k, e in enumerate(E)])
+    scale = np.abs(ref).max()
+    assert np.abs(y64 - ref).max() <= 1e-12 * scale
+    x32 = x64.to(torch.complex64)
+    y32 = ctx.apply(E, x32, B.RSN_MIXED).cpu().numpy()
+    ref32 = np.stack([O.apply_operator(j, e, x32[k].cpu().numpy().astype(np.complex128)) for k, e in enumerate(E)])
+    assert np.abs(y32 - ref32).max() <= 2e-6 * scale
+    ctx.close()
+
+
+def test_solve_columns_fp64_matches_lu(B):
+    j = JUNCTIONS["junction_R4"]()
+    E = [0.17, 0.23]
+    cols = j.right_columns()[::37]
+    ctx = B.Context(0).set_junction(j)
+    x, iters, relres = ctx.solve_columns(E, cols, B.default_opts(B.RSN_FP64))
+    x = x.cpu().numpy()
+    for e, En in enumerate(E):
+        ref = O.solve_columns(j, En, cols).T
+        err = np.linalg.norm(x[e] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() <= 1e-9, err.max()
+    assert np.all(iters > 0) and np.all(relres <= 1e-13)
+    ctx.close()
+
+
+def test_solve_columns_mixed_residual_and_ragged_tiles(B):
+    j = JUNCTIONS["ragged_R3"]()
+    E = [0.05, 0.31]
+    cols = j.right_columns()[::11]
+    ctx = B.Context(0).set_junction(j)
+    ctx.set_tiling(4, 6, 2)
+    x, iters, relres = ctx.solve_columns(E, cols, B.default_opts(B.RSN_MIXED))
+    x = x.cpu().numpy()
+    for e, En in enumerate(E):
+        b = np.zeros((j.N, cols.size), complex)
+        b[cols, np.arange(cols.size)] = 1
+        r = b - O.apply_operator(j, En, x[e].T)
+        assert (np.linalg.norm(r, axis=0) <= 1.5e-10).all()
+        ref = O.solve_columns(j, En, cols).T
+        err = np.linalg.norm(x[e] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() <= 1e-6
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_waveguide_transmission_and_staircase(B, prec):
+    w = P.waveguide()
+    E = P.energy_grid(0.05, 2.0, 64)[::4]
+    ctx = B.Context(0).set_junction(w)
+    p = B.RSN_FP64 if prec == "fp64" else B.RSN_MIXED
+    T = ctx.transmission(E, None, B.default_opts(p))
+    T_ref = O.transmission(w, E)
+    if prec == "fp64":
+        assert np.all(np.abs(T - T_ref) <= 1e-9 * np.maximum(np.abs(T_ref), 1e-3))
+    else:
+        assert np.all(np.abs(T - T_ref) <= 1e-6)
+    th = O.channel_thresholds(8, 8, 0.5)
+    for e, t in zip(E, T):
+        below = th[th < e]
+        if (below.size and e - below.max() >= 0.18) or (not below.size and th.min() - e >= 0.06):
+            assert abs(t - O.open_channels(8, 8, 0.5, e)) <= 0.06
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_vjp_matches_oracle_gradient(B, prec):
+    j = JUNCTIONS["junction_R4"]()
+    E = [0.16, 0.2, 0.24]
+    Tb = [1.0, -0.5, 2.0]
+    cols = j.right_columns()[::13]
+    ctx = B.Context(0).set_junction(j)
+    p = B.RSN_FP64 if prec == "fp64" else B.RSN_MIXED
+    T, g = ctx.transmission_vjp(E, Tb, cols, B.default_opts(p))
+    T_ref, g_ref = O.transmission_grad(j, E, cols, T_bar=Tb)
+    gs = np.abs(g_ref).max()
+    if prec == "fp64":
+        assert np.all(np.abs(T - T_ref) <= 1e-9 * np.maximum(np.abs(T_ref), 1e-3))
+        assert np.abs(g - g_ref).max() <= 1e-8 * gs
+    else:
+        assert np.all(np.abs(T - T_ref) <= 1e-6)
+        assert np.abs(g - g_ref).max() <= 1e-5 * gs
+    ctx.close()
+
+
+def test_fp64_is_bit_reproducible(B):
+    j = JUNCTIONS["junction_R4"]()
+    cols = j.right_columns()[::29]
+    ctx = B.Context(0).set_junction(j)
+    T1 = ctx.transmission([0.2, 0.21], cols, B.default_opts(B.RSN_FP64))
+    T2 = ctx.transmission([0.2, 0.21], cols, B.default_opts(B.RSN_FP64))
+    assert np.array_equal(T1, T2)
+    ctx.close()
