@@ -69,17 +69,24 @@ typedef struct {
                            RSN_MIXED: complex FP32 recurrence on the correction
                            equation, FP64 true residual / update / T sums. */
     double tol;         /* stop when ||b - A x||_2 <= tol * ||b||_2 (true residual, FP64) */
-    double tol_inner;   /* each refinement sweep reduces its recurrence residual by this factor */
-    int max_iter;       /* cap on Krylov iterations per refinement sweep */
-    int max_outer;      /* cap on refinement sweeps */
+    double tol_inner;   /* reliable-update factor (0 < tol_inner < 1): once the recurrence
+                           residual has dropped by this factor since the last true residual,
+                           the FP64 true residual b - A x replaces it (the search direction is
+                           kept) or, if below tol, finishes the system */
+    int max_iter;       /* cap on Krylov iterations per system */
+    int max_outer;      /* cap on true-residual replacements per system */
     double deadline_ms; /* wall-clock budget of the call, 0 = none */
-    int rhs_block;      /* systems solved concurrently (0 = choose from free memory) */
+    int rhs_block;      /* slots: systems solved concurrently (0 = automatic); the
+                           remaining systems wait in a queue and take freed slots */
     int use_graph;      /* 1: replay the iteration body as a captured CUDA graph */
-    int graph_iters;    /* iterations per graph replay between convergence polls */
+    int graph_iters;    /* iterations per graph replay between convergence polls (1..256) */
+    int timing;         /* 1: time every COCG operator / update launch with CUDA events
+                           (read back with rsn_kernel_stats) */
 } rsn_solver_opts;
 
-/* Defaults for a precision: FP64 -> tol 1e-13, tol_inner 1e-11;
-   MIXED -> tol 1e-10, tol_inner 1e-5; max_iter 4000, max_outer 8, graphs on. */
+/* Defaults for a precision: FP64 -> tol 1e-13, tol_inner 1e-6;
+   MIXED -> tol 1e-10, tol_inner 1e-1; max_iter 20000, max_outer 64,
+   graphs on (16 iterations per replay), timing off. */
 void rsn_default_opts(int precision, rsn_solver_opts* opts);
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`
@@ -158,6 +165,37 @@ rsn_status rsn_transmission_vjp(rsn_ctx* ctx, int n_e, const double* E, int n_co
    milliseconds of the solve phase.  Any pointer may be NULL. */
 rsn_status rsn_last_stats(const rsn_ctx* ctx, int64_t* krylov_iters, int64_t* sweeps,
                           int64_t* launches, double* gpu_ms);
+
+/* Live per-kernel timing of the last solve call made with opts.timing = 1.
+   kind 0: the fused COCG operator kernel (p = r + beta p, q = A p, p^T q);
+   kind 1: the COCG update kernel (r -= alpha q, d += alpha p, r^T r).
+   launches: launches timed; ms: summed CUDA-event durations on the library's
+   stream; bytes: algorithmic HBM bytes of those launches (vectors read and
+   written once per active system: 4 vectors for kind 0, 6 for kind 1).
+   Any output pointer may be NULL.  Errors: RSN_EINVAL (kind). */
+rsn_status rsn_kernel_stats(const rsn_ctx* ctx, int kind, int64_t* launches, double* ms,
+                            double* bytes);
+
+/* Micro-benchmark of one kernel of the COCG iteration on `nslots` systems of
+   the current junction, all active with a synthetic finite state (results are
+   meaningless, timings are not).  kind 0: fused operator kernel (p update,
+   stencil, V/CAP, projectors, p^T A p); kind 1: COCG update kernel; kind 2:
+   FP64 true-residual kernel.  Runs 2 untimed then `reps` timed launches on the
+   context's stream (CUDA events).  ms_per_launch: mean duration;
+   bytes_per_launch: algorithmic HBM bytes of one launch (each vector read or
+   written once per point).  Errors: RSN_ESTATE, RSN_EINVAL, RSN_ENOMEM. */
+rsn_status rsn_bench_kernel(rsn_ctx* ctx, int precision, int kind, int nslots, int reps,
+                            double* ms_per_launch, double* bytes_per_launch);
+
+/* Autotuner: times the fused operator kernel (rsn_bench_kernel kind 0) for a
+   set of tilings of this grid -- the plane-streaming (bulk-copy) kernel with
+   several z-chunk lengths, and the register-prefetch kernel over rows per tile,
+   points per thread and z-chunks -- and keeps the fastest on the context.
+   Outputs (any may be NULL): the chosen TY, Lz, ppt (0 = automatic), tma (1 if
+   the plane-streaming kernel won) and its algorithmic GB/s.  Errors: as
+   rsn_bench_kernel; RSN_ECUDA if no candidate ran. */
+rsn_status rsn_autotune(rsn_ctx* ctx, int precision, int nslots, int* TY, int* Lz, int* ppt,
+                        int* tma, double* best_gbs);
 
 /* Override the operator kernel's tile (0 = automatic): TY rows of the x-y
    plane per CTA, Lz planes per CTA along z, ppt owned points per thread

@@ -40,7 +40,11 @@ _SIGS = {
                                         ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
     "rsn_last_stats": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_last_error": (ct.c_char_p, [ct.c_void_p]),
+    "rsn_kernel_stats": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_set_tiling": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int]),
+    "rsn_bench_kernel": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]),
+    "rsn_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                ct.c_void_p]),
 }
 
 
@@ -57,6 +61,7 @@ class SolverOpts(ct.Structure):
         ("rhs_block", ct.c_int),
         ("use_graph", ct.c_int),
         ("graph_iters", ct.c_int),
+        ("timing", ct.c_int),
     ]
 
 
@@ -234,6 +239,27 @@ class Context:
                     self.lib.rsn_transmission_vjp(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
                                                   ct.byref(opts), _ptr(Tb), dptr, isdev, _ptr(T)))
         return T, dV
+
+    def kernel_stats(self, kind: int):
+        """(launches, ms, algorithmic bytes) of kind 0 (COCG operator) / 1 (COCG update)."""
+        la, ms, by = ct.c_int64(), ct.c_double(), ct.c_double()
+        self._check("rsn_kernel_stats", self.lib.rsn_kernel_stats(self.h, kind, ct.byref(la), ct.byref(ms),
+                                                                  ct.byref(by)))
+        return {"launches": la.value, "ms": ms.value, "bytes": by.value}
+
+    def bench_kernel(self, precision: int, kind: int, nslots: int, reps: int = 20):
+        """(ms per launch, algorithmic bytes per launch) of one COCG kernel in isolation."""
+        ms, by = ct.c_double(), ct.c_double()
+        self._check("rsn_bench_kernel", self.lib.rsn_bench_kernel(self.h, precision, kind, nslots, reps,
+                                                                  ct.byref(ms), ct.byref(by)))
+        return ms.value, by.value
+
+    def autotune(self, precision: int, nslots: int):
+        """Pick the fastest operator-kernel tiling; returns the choice and its GB/s."""
+        ty, lz, ppt, tma, gbs = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int(), ct.c_double()
+        self._check("rsn_autotune", self.lib.rsn_autotune(self.h, precision, nslots, ct.byref(ty), ct.byref(lz),
+                                                          ct.byref(ppt), ct.byref(tma), ct.byref(gbs)))
+        return {"TY": ty.value, "Lz": lz.value, "ppt": ppt.value, "tma": tma.value, "gbs": gbs.value}
 
     def last_stats(self):
         it, sw, la, ms = ct.c_int64(), ct.c_int64(), ct.c_int64(), ct.c_double()

@@ -1,21 +1,15 @@
 // C-ABI entry points, device-side setup of the operator data, and the host
-// driver of the batched COCG solve with FP64 iterative refinement.
+// driver of the streaming COCG solver with FP64 reliable updates.
 //
-// Solve schedule for one batch of systems A(E_s) x_s = b_s (all in one stream):
-//   repeat (refinement sweep):
-//     [project x64 + d]  -> c_x                    (projector gathers, FP64)
-//     op(RESID)          -> r = b - A(x64 + d), ||r||^2, r^T r   (FP64 arithmetic)
-//     x_update           -> x64 += d, d = 0
-//     outer_book         -> converged?  else restart the inner solve on r
-//     [project r]        -> c_r
-//     repeat (captured CUDA graph of `graph_iters` COCG iterations):
-//        op(COCG)    p = r + beta p ; q = A p ; partial mu = p^T q
-//        cocg_update alpha = rho/mu ; r -= alpha q ; d += alpha p ; partial rho, ||r||^2
-//        [project r] -> c_r for the next iteration
-//        inner_book  iteration counts, convergence, breakdown, active count
-//     until no inner solve is active
-//   until no system is active
-// The host reads one integer per graph replay; everything else stays on the GPU.
+// Systems A(E_k) x_k = b_k wait in a queue; a fixed pool of S slots holds the
+// ones being solved.  One iteration of the solver is a fixed sequence of
+// kernels (see vec_kernels.cu): new systems are initialised, systems whose
+// recurrence reached its target get an FP64 true residual (which either
+// finishes them or replaces the recurrence residual, keeping the search
+// direction), finished slots take the next queued systems, and every active
+// slot does one COCG iteration.  `graph_iters` iterations are captured once as
+// a CUDA graph and replayed; between replays the host reads a few integers
+// (queue position, busy slots).  Everything else stays on the GPU.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -63,25 +57,33 @@ struct DevBuf {
 struct Tiling {
   int TY = 0, Lz = 0, ytiles = 0, ztiles = 0, n = 0, ppt = 1, threads = 32;
   size_t smem = 0;
+  bool tma = false;  // whole-plane tile streamed by bulk copies (op_kernel_tma)
 };
 
+// Slot pool of the streaming solver (sized for S slots of N points).
 struct Workspace {
   int slots = 0;
   bool fp32 = false;
-  bool adjoint = false;
   long long N = 0;
   int PA = 0, PB = 0, n_proj = 0;
-  DevBuf X0, X1, r, p0, p1, q, d;
-  DevBuf junc, E, col, voff, iters, done, outer_done, total_iters, n_outer, status, breakdowns;
-  DevBuf bnorm2, tol2, relres, out_index, wt;
-  DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, n_active;
+  DevBuf Xslot, r, p0, p1, q, d;
+  DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, rho_cur, beta_cur;
+  DevBuf bnorm2, rlast2, tol2;
+  DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters;
   int generation = 0;
 };
 
+// Per-call system queue and outputs.
+struct CallBufs {
+  DevBuf sys_junc, sys_E, sys_col, sys_xo, sys_xfo, sys_dep, out_iters, out_relres, out_status, out_t;
+  DevBuf X0, X1, wt, g, t_all, gr_cols, Td;
+};
+
 struct GraphKey {
-  int fp32, slots, iters, generation, proj;
+  int fp32, slots, iters, generation, proj, timing;
   bool operator<(const GraphKey& o) const {
-    return std::tie(fp32, slots, iters, generation, proj) < std::tie(o.fp32, o.slots, o.iters, o.generation, o.proj);
+    return std::tie(fp32, slots, iters, generation, proj, timing) <
+           std::tie(o.fp32, o.slots, o.iters, o.generation, o.proj, o.timing);
   }
 };
 
@@ -113,13 +115,19 @@ struct rsn_ctx {
   DevBuf jd;  // device JuncDev (one per launch configuration, uploaded before a batch)
 
   Workspace ws;
+  CallBufs cb;
+  DevBuf bd;  // device BatchDev: [0] streaming solver, [1] rsn_apply
   std::map<GraphKey, cudaGraphExec_t> graphs;
-  int* n_active_host = nullptr;  // pinned
+  int* sched_host = nullptr;  // pinned mirror of BatchDev::sched
 
   // stats of the last solve
   int64_t st_iters = 0, st_sweeps = 0, st_launches = 0;
   double st_ms = 0.0;
-  int tile_override[4] = {0, 0, 0, 0};  // TY, Lz, ppt, unused (autotuner / tests)
+  // live kernel timing (opts.timing): [0] COCG operator kernel, [1] COCG update kernel
+  std::vector<cudaEvent_t> tev;  // 4 per graph iteration
+  int64_t ks_launches[2] = {0, 0};
+  double ks_ms[2] = {0, 0}, ks_bytes[2] = {0, 0};
+  int tile_override[4] = {0, 0, 0, 0};  // TY, Lz, ppt, no-TMA (autotuner / tests)
 };
 
 static std::string g_create_err;
@@ -198,6 +206,19 @@ static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslo
   t.ztiles = (nz + t.Lz - 1) / t.Lz;
   t.n = t.ytiles * t.ztiles;
   t.smem = op_smem_bytes(!compute64, mode, R, TY, nx, c->n_proj);
+  // plane-streaming kernel: FP32 COCG / apply on whole planes whose byte sizes
+  // keep every bulk copy 16-byte aligned; an explicit TY or ppt selects the
+  // register-prefetch kernel instead
+  const long long pl = (long long)nx * ny;
+  if (!compute64 && mode != OP_RESID && t.ytiles == 1 && pl <= 1024 && (pl * 8) % 16 == 0 &&
+      (c->N * 8) % 16 == 0 && c->tile_override[0] == 0 && c->tile_override[2] == 0 && c->tile_override[3] == 0) {
+    const size_t sm = op_tma_smem_bytes(true, mode, R, nx, ny, c->n_proj);
+    if (sm <= 200 * 1024) {
+      t.tma = true;
+      t.smem = sm;
+      t.threads = (int)((pl + 31) / 32 * 32);
+    }
+  }
   return t;
 }
 
@@ -217,7 +238,8 @@ static rsn_status commit_setup(rsn_ctx* c) {
   std::vector<float2> dgf(N);
   for (long long i = 0; i < N; ++i) {
     dg[i] = make_double2(-c->v[i] + 3.0 * cw[0] * ih2, c->gl[i] + c->gr[i]);
-    dgf[i] = make_float2((float)dg[i].x, (float)dg[i].y);
+    // FP32 kernels use the difference form of the stencil: no FD diagonal here
+    dgf[i] = make_float2((float)(-c->v[i]), (float)dg[i].y);
   }
   RSN_CUDA(c, c->dg64.ensure(N * sizeof(double2)));
   RSN_CUDA(c, c->dg32.ensure(N * sizeof(float2)));
@@ -374,17 +396,18 @@ void rsn_default_opts(int precision, rsn_solver_opts* o) {
   o->precision = precision == RSN_MIXED ? RSN_MIXED : RSN_FP64;
   if (o->precision == RSN_MIXED) {
     o->tol = 1e-10;
-    o->tol_inner = 1e-5;
+    o->tol_inner = 1e-1;
   } else {
     o->tol = 1e-13;
-    o->tol_inner = 1e-11;
+    o->tol_inner = 1e-6;
   }
-  o->max_iter = 4000;
-  o->max_outer = 8;
+  o->max_iter = 20000;
+  o->max_outer = 64;
   o->deadline_ms = 0.0;
   o->rhs_block = 0;
   o->use_graph = 1;
   o->graph_iters = 16;
+  o->timing = 0;
 }
 
 rsn_status rsn_create(rsn_ctx** out, int device, void* cuda_stream) {
@@ -412,7 +435,7 @@ rsn_status rsn_create(rsn_ctx** out, int device, void* cuda_stream) {
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
-      cudaMallocHost(&c->n_active_host, 4 * sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&c->sched_host, (3 + 2 * kMaxGraphIters) * sizeof(int)) != cudaSuccess) {
     g_create_err = "rsn_create: stream/event/pinned allocation failed";
     rsn_destroy(c);
     return RSN_ECUDA;
@@ -427,7 +450,8 @@ rsn_status rsn_destroy(rsn_ctx* c) {
   cudaSetDevice(c->device);
   if (c->st) cudaStreamSynchronize(c->st);
   clear_graphs(c);
-  if (c->n_active_host) cudaFreeHost(c->n_active_host);
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  if (c->sched_host) cudaFreeHost(c->sched_host);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->t0) cudaEventDestroy(c->t0);
@@ -526,6 +550,14 @@ rsn_status rsn_set_projectors(rsn_ctx* c, int n_proj, const int64_t* off, const 
 
 const char* rsn_last_error(const rsn_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
+rsn_status rsn_kernel_stats(const rsn_ctx* c, int kind, int64_t* launches, double* ms, double* bytes) {
+  if (!c || kind < 0 || kind > 1) return RSN_EINVAL;
+  if (launches) *launches = c->ks_launches[kind];
+  if (ms) *ms = c->ks_ms[kind];
+  if (bytes) *bytes = c->ks_bytes[kind];
+  return RSN_OK;
+}
+
 rsn_status rsn_last_stats(const rsn_ctx* c, int64_t* it, int64_t* sw, int64_t* la, double* ms) {
   if (!c) return RSN_EINVAL;
   if (it) *it = c->st_iters;
@@ -553,70 +585,78 @@ static rsn_status leave(rsn_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------
-// workspace
+// slot pool
 // ---------------------------------------------------------------------------
-static size_t per_slot_bytes(const rsn_ctx* c, bool fp32, bool adjoint) {
+static size_t slot_bytes(const rsn_ctx* c, bool fp32) {
   const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
-  return (size_t)c->N * (sizeof(double2) * (adjoint ? 2 : 1) + 5 * el) + 4096;
+  return (size_t)c->N * (sizeof(double2) + 5 * el) + 8192;
 }
 
-static int choose_slots(rsn_ctx* c, const rsn_solver_opts* o, bool adjoint, long long total) {
-  if (o->rhs_block > 0) return (int)std::min<long long>(o->rhs_block, total);
+// Slots: enough systems in flight to fill the GPU, few enough (relative to the
+// queue) that the drain at the end of the queue stays short, and within memory.
+static int choose_slots(rsn_ctx* c, const rsn_solver_opts* o, long long nsys, size_t reserved) {
+  if (o->rhs_block > 0) return (int)std::max<long long>(1, std::min<long long>(o->rhs_block, nsys));
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
-  const size_t per = per_slot_bytes(c, o->precision == RSN_MIXED, adjoint);
-  long long cap = (long long)(0.5 * (double)fr / (double)per);
-  cap = std::max<long long>(1, std::min<long long>(cap, 16384));
-  return (int)std::min<long long>(cap, total);
+  const double avail = fr > reserved ? 0.6 * (double)(fr - reserved) : 0.0;
+  long long cap = (long long)(avail / (double)slot_bytes(c, o->precision == RSN_MIXED));
+  cap = std::max<long long>(1, std::min<long long>(cap, 8192));
+  long long want = std::max<long long>(512, std::min<long long>(2048, nsys / 4));
+  want = std::min(want, nsys);
+  return (int)std::max<long long>(1, std::min(want, cap));
 }
 
-static rsn_status ensure_ws(rsn_ctx* c, bool fp32, bool adjoint, int slots, bool own_x0) {
+static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   Workspace& w = c->ws;
   const long long N = c->N;
-  const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
-  const Tiling ti = choose_tiling(c, !fp32, OP_COCG, slots), tr = choose_tiling(c, true, OP_RESID, slots);
+  const Tiling ti = choose_tiling(c, !fp32, OP_COCG, S), tr = choose_tiling(c, true, OP_RESID, S);
   const int PA = std::max(ti.n, tr.n), PB = c->jh.nB;
-  const bool same = w.slots == slots && w.fp32 == fp32 && w.N == N && w.PA == PA && w.PB == PB &&
-                    w.n_proj == c->n_proj && (!adjoint || w.adjoint);
-  if (same && (!own_x0 || w.X0.n >= (size_t)slots * N * sizeof(double2))) return RSN_OK;
-  const size_t vb = (size_t)slots * N;
-  if (own_x0) RSN_CUDA(c, w.X0.ensure(vb * sizeof(double2)));
-  if (adjoint) RSN_CUDA(c, w.X1.ensure(vb * sizeof(double2)));
+  if (w.slots == S && w.fp32 == fp32 && w.N == N && w.PA == PA && w.PB == PB && w.n_proj == c->n_proj)
+    return RSN_OK;
+  const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
+  const size_t vb = (size_t)S * N;
+  RSN_CUDA(c, w.Xslot.ensure(vb * sizeof(double2)));
   RSN_CUDA(c, w.r.ensure(vb * el));
   RSN_CUDA(c, w.p0.ensure(vb * el));
   RSN_CUDA(c, w.p1.ensure(vb * el));
   RSN_CUDA(c, w.q.ensure(vb * el));
   RSN_CUDA(c, w.d.ensure(vb * el));
-  const size_t si = slots * sizeof(int), sd = slots * sizeof(double);
+  const size_t si = S * sizeof(int), sd = S * sizeof(double), sl = S * sizeof(long long);
+  RSN_CUDA(c, w.state.ensure(si));
+  RSN_CUDA(c, w.sys.ensure(si));
   RSN_CUDA(c, w.junc.ensure(si));
   RSN_CUDA(c, w.E.ensure(sd));
   RSN_CUDA(c, w.col.ensure(si));
-  RSN_CUDA(c, w.voff.ensure(slots * sizeof(long long)));
+  RSN_CUDA(c, w.voff.ensure(sl));
+  RSN_CUDA(c, w.xo.ensure(sl));
+  RSN_CUDA(c, w.xfo.ensure(sl));
   RSN_CUDA(c, w.iters.ensure(si));
-  RSN_CUDA(c, w.done.ensure(si));
-  RSN_CUDA(c, w.outer_done.ensure(si));
   RSN_CUDA(c, w.total_iters.ensure(si));
-  RSN_CUDA(c, w.n_outer.ensure(si));
-  RSN_CUDA(c, w.status.ensure(si));
-  RSN_CUDA(c, w.breakdowns.ensure(si));
+  RSN_CUDA(c, w.cyc_iters.ensure(si));
+  RSN_CUDA(c, w.n_upd.ensure(si));
+  RSN_CUDA(c, w.restart.ensure(si));
+  RSN_CUDA(c, w.rho_cur.ensure(S * sizeof(double2)));
+  RSN_CUDA(c, w.beta_cur.ensure(S * sizeof(double2)));
   RSN_CUDA(c, w.bnorm2.ensure(sd));
+  RSN_CUDA(c, w.rlast2.ensure(sd));
   RSN_CUDA(c, w.tol2.ensure(sd));
-  RSN_CUDA(c, w.relres.ensure(sd));
-  RSN_CUDA(c, w.out_index.ensure(si));
-  RSN_CUDA(c, w.wt.ensure(sd));
-  RSN_CUDA(c, w.rho0.ensure((size_t)slots * PA * sizeof(double2)));
-  RSN_CUDA(c, w.nrm0.ensure((size_t)slots * PA * sizeof(double)));
-  RSN_CUDA(c, w.mu.ensure((size_t)slots * PA * sizeof(double2)));
-  RSN_CUDA(c, w.rho.ensure(2 * (size_t)slots * PB * sizeof(double2)));
-  RSN_CUDA(c, w.nrm.ensure((size_t)slots * PB * sizeof(double)));
+  RSN_CUDA(c, w.rho0.ensure((size_t)S * PA * sizeof(double2)));
+  RSN_CUDA(c, w.nrm0.ensure((size_t)S * PA * sizeof(double)));
+  RSN_CUDA(c, w.mu.ensure((size_t)S * PA * sizeof(double2)));
+  RSN_CUDA(c, w.rho.ensure((size_t)S * PB * sizeof(double2)));
+  RSN_CUDA(c, w.nrm.ensure((size_t)S * PB * sizeof(double)));
   const size_t npj = std::max(1, c->n_proj);
-  RSN_CUDA(c, w.c_r.ensure((size_t)slots * npj * sizeof(double2)));
-  RSN_CUDA(c, w.c_p.ensure(2 * (size_t)slots * npj * sizeof(double2)));
-  RSN_CUDA(c, w.c_x.ensure((size_t)slots * npj * sizeof(double2)));
-  RSN_CUDA(c, w.n_active.ensure(4 * sizeof(int)));
-  w.slots = slots;
+  RSN_CUDA(c, w.c_r.ensure((size_t)S * npj * sizeof(double2)));
+  RSN_CUDA(c, w.c_p.ensure(2 * (size_t)S * npj * sizeof(double2)));
+  RSN_CUDA(c, w.c_x.ensure((size_t)S * npj * sizeof(double2)));
+  RSN_CUDA(c, w.sched.ensure((3 + 2 * kMaxGraphIters) * sizeof(int)));
+  RSN_CUDA(c, w.counters.ensure(4 * sizeof(unsigned long long)));
+  std::vector<long long> hvo(S);
+  for (int s = 0; s < S; ++s) hvo[s] = (long long)s * N;
+  RSN_CUDA(c, cudaMemcpy(w.voff.p, hvo.data(), sl, cudaMemcpyHostToDevice));
+  RSN_CUDA(c, c->bd.ensure(2 * sizeof(BatchDev)));
+  w.slots = S;
   w.fp32 = fp32;
-  w.adjoint = w.adjoint || adjoint;
   w.N = N;
   w.PA = PA;
   w.PB = PB;
@@ -626,34 +666,77 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, bool adjoint, int slots, bool
   return RSN_OK;
 }
 
-static BatchDev batch_view(rsn_ctx* c, double2* x64, const double2* xf) {
+static rsn_status ensure_calls(rsn_ctx* c, long long nsys) {
+  CallBufs& q = c->cb;
+  const size_t n = (size_t)std::max<long long>(1, nsys);
+  RSN_CUDA(c, q.sys_junc.ensure(n * sizeof(int)));
+  RSN_CUDA(c, q.sys_E.ensure(n * sizeof(double)));
+  RSN_CUDA(c, q.sys_col.ensure(n * sizeof(int)));
+  RSN_CUDA(c, q.sys_xo.ensure(n * sizeof(long long)));
+  RSN_CUDA(c, q.sys_xfo.ensure(n * sizeof(long long)));
+  RSN_CUDA(c, q.sys_dep.ensure(n * sizeof(int)));
+  RSN_CUDA(c, q.out_iters.ensure(n * sizeof(int)));
+  RSN_CUDA(c, q.out_relres.ensure(n * sizeof(double)));
+  RSN_CUDA(c, q.out_status.ensure(n * sizeof(int)));
+  RSN_CUDA(c, q.out_t.ensure(n * sizeof(double)));
+  return RSN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the streaming solver
+// ---------------------------------------------------------------------------
+struct StreamIn {
+  std::vector<int> junc, col, dep;
+  std::vector<double> E;
+  std::vector<long long> xo, xfo;
+  void resize(size_t n) {
+    junc.assign(n, 0);
+    col.assign(n, 0);
+    dep.assign(n, -1);
+    E.assign(n, 0.0);
+    xo.assign(n, -1);
+    xfo.assign(n, 0);
+  }
+};
+struct StreamOut {
+  std::vector<int> iters, status;
+  std::vector<double> relres;
+  bool timeout = false;
+  unsigned long long krylov = 0, updates = 0;
+};
+
+// BatchDev view of the slot pool (per-call system queue fields left empty).
+static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   Workspace& w = c->ws;
   BatchDev b;
   memset(&b, 0, sizeof(b));
-  b.nslots = w.slots;
+  b.nslots = S;
   b.PA = w.PA;
   b.PB = w.PB;
+  b.state = w.state.as<int>();
+  b.sys = w.sys.as<int>();
   b.junc = w.junc.as<int>();
   b.E = w.E.as<double>();
   b.col = w.col.as<int>();
   b.voff = w.voff.as<long long>();
-  b.x64 = x64;
-  b.xf = xf;
+  b.xo = w.xo.as<long long>();
+  b.xfo = w.xfo.as<long long>();
+  b.iters = w.iters.as<int>();
+  b.total_iters = w.total_iters.as<int>();
+  b.cyc_iters = w.cyc_iters.as<int>();
+  b.n_upd = w.n_upd.as<int>();
+  b.restart = w.restart.as<int>();
+  b.rho_cur = w.rho_cur.as<double2>();
+  b.beta_cur = w.beta_cur.as<double2>();
+  b.bnorm2 = w.bnorm2.as<double>();
+  b.rlast2 = w.rlast2.as<double>();
+  b.tol2 = w.tol2.as<double>();
+  b.x64 = w.Xslot.as<double2>();
   b.r = w.r.p;
   b.p0 = w.p0.p;
   b.p1 = w.p1.p;
   b.q = w.q.p;
   b.d = w.d.p;
-  b.iters = w.iters.as<int>();
-  b.done = w.done.as<int>();
-  b.outer_done = w.outer_done.as<int>();
-  b.total_iters = w.total_iters.as<int>();
-  b.n_outer = w.n_outer.as<int>();
-  b.status = w.status.as<int>();
-  b.breakdowns = w.breakdowns.as<int>();
-  b.bnorm2 = w.bnorm2.as<double>();
-  b.tol2 = w.tol2.as<double>();
-  b.relres = w.relres.as<double>();
   b.rho0_part = w.rho0.as<double2>();
   b.nrm0_part = w.nrm0.as<double>();
   b.rho_part = w.rho.as<double2>();
@@ -662,96 +745,117 @@ static BatchDev batch_view(rsn_ctx* c, double2* x64, const double2* xf) {
   b.c_r = w.c_r.p;
   b.c_p = w.c_p.p;
   b.c_x = w.c_x.as<double2>();
-  b.n_active = w.n_active.as<int>();
+  b.sched = w.sched.as<int>();
+  b.counters = w.counters.as<unsigned long long>();
+  b.tol = o->tol;
+  b.delta = o->tol_inner;
+  b.max_iter = o->max_iter;
+  b.max_upd = o->max_outer;
+  b.cycle_cap = std::max(32, std::min(o->max_iter, 400));
   return b;
 }
 
-// ---------------------------------------------------------------------------
-// one batch: systems [0, nact) of the workspace, slot s with energy E[s] and
-// right-hand side col[s] (>= 0: unit vector, -1: adjoint from xf)
-// ---------------------------------------------------------------------------
-struct BatchResult {
-  std::vector<int> total_iters, status, outer_done, n_outer;
-  std::vector<double> relres;
-  bool timeout = false;
-};
-
-static rsn_status run_batch(rsn_ctx* c, const rsn_solver_opts* o, int nact, const double* E, const int* col,
-                            double2* x64, const double2* xf, std::chrono::steady_clock::time_point t_start,
-                            BatchResult& res) {
-  Workspace& w = c->ws;
-  const int S = w.slots;
+static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamIn& in, double2* x64_base,
+                             const double2* xf_base, bool want_t, size_t reserved,
+                             std::chrono::steady_clock::time_point t_start, StreamOut& out) {
+  const long long nsys = (long long)in.E.size();
   const bool fp32 = o->precision == RSN_MIXED;
-  const long long N = c->N;
+  const int S = choose_slots(c, o, nsys, reserved);
+  rsn_status rs = ensure_ws(c, fp32, S);
+  if (rs != RSN_OK) return rs;
+  if ((rs = ensure_calls(c, nsys)) != RSN_OK) return rs;
+  Workspace& w = c->ws;
+  CallBufs& q = c->cb;
   cudaStream_t st = c->st;
-  // per-slot inputs
-  std::vector<double> hE(S, 0.0), hb(S, 1.0);
-  std::vector<int> hcol(S, 0), hj(S, 0), hdone(S, 1), hzero(S, 0);
-  std::vector<long long> hvo(S, 0);
-  for (int s = 0; s < S; ++s) {
-    hvo[s] = (long long)s * N;
-    if (s < nact) {
-      hE[s] = E[s];
-      hcol[s] = col[s];
-      hdone[s] = 0;
-    }
-  }
-  RSN_CUDA(c, cudaMemcpyAsync(w.E.p, hE.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.col.p, hcol.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.junc.p, hj.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.voff.p, hvo.data(), S * sizeof(long long), cudaMemcpyHostToDevice, st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.done.p, hdone.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.outer_done.p, hdone.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.bnorm2.p, hb.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
-  RSN_CUDA(c, cudaMemsetAsync(w.iters.p, 0, S * sizeof(int), st));
-  RSN_CUDA(c, cudaMemsetAsync(w.total_iters.p, 0, S * sizeof(int), st));
-  RSN_CUDA(c, cudaMemsetAsync(w.n_outer.p, 0, S * sizeof(int), st));
-  RSN_CUDA(c, cudaMemsetAsync(w.status.p, 0, S * sizeof(int), st));
-  RSN_CUDA(c, cudaMemsetAsync(w.breakdowns.p, 0, S * sizeof(int), st));
-  RSN_CUDA(c, cudaMemsetAsync(w.relres.p, 0, S * sizeof(double), st));
-  const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
-  RSN_CUDA(c, cudaMemsetAsync(x64, 0, (size_t)nact * N * sizeof(double2), st));
-  RSN_CUDA(c, cudaMemsetAsync(w.d.p, 0, (size_t)S * N * el, st));
+  const long long N = c->N;
+  // system queue
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_junc.p, in.junc.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_E.p, in.E.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_col.p, in.col.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_xo.p, in.xo.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_xfo.p, in.xfo.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_dep.p, in.dep.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemsetAsync(q.out_status.p, 0xff, nsys * sizeof(int), st));
+  RSN_CUDA(c, cudaMemsetAsync(q.out_iters.p, 0, nsys * sizeof(int), st));
+  RSN_CUDA(c, cudaMemsetAsync(q.out_relres.p, 0, nsys * sizeof(double), st));
+  if (want_t) RSN_CUDA(c, cudaMemsetAsync(q.out_t.p, 0, nsys * sizeof(double), st));
+  // slot pool starts empty
+  RSN_CUDA(c, cudaMemsetAsync(w.state.p, 0, S * sizeof(int), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.sched.p, 0, (3 + 2 * kMaxGraphIters) * sizeof(int), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.counters.p, 0, 4 * sizeof(unsigned long long), st));
+
+  BatchDev b = slot_batch(c, S, o);
+  b.x64 = x64_base ? x64_base : w.Xslot.as<double2>();
+  b.xf = xf_base;
+  b.nsys = (int)nsys;
+  b.sys_junc = q.sys_junc.as<int>();
+  b.sys_E = q.sys_E.as<double>();
+  b.sys_col = q.sys_col.as<int>();
+  b.sys_xo = q.sys_xo.as<long long>();
+  b.sys_xfo = q.sys_xfo.as<long long>();
+  b.sys_dep = q.sys_dep.as<int>();
+  b.out_iters = q.out_iters.as<int>();
+  b.out_relres = q.out_relres.as<double>();
+  b.out_status = q.out_status.as<int>();
+  b.out_t = want_t ? q.out_t.as<double>() : nullptr;
+  RSN_CUDA(c, cudaMemcpyAsync(c->bd.p, &b, sizeof(b), cudaMemcpyHostToDevice, st));
+  const BatchDev* bdev = c->bd.as<BatchDev>();
 
   LaunchCfg cfg;
-  rsn_status rs = make_cfg(c, fp32, S, cfg);
-  if (rs != RSN_OK) return rs;
-  const BatchDev b = batch_view(c, x64, xf);
+  if ((rs = make_cfg(c, fp32, S, cfg)) != RSN_OK) return rs;
   const JuncDev* ji = cfg.jt_inner;
   const JuncDev* jr = cfg.jt_resid;
   const int nB = c->jh.nB;
   const bool proj = c->n_proj > 0;
   const dim3 gi(cfg.inner.n, S), gr(cfg.resid.n, S);
-  int64_t launches = 0;
-
-  if (xf) {
-    RSN_CUDA(c, launch_bnorm_adjoint(S, st, jr, b));
-    ++launches;
+  const int G = std::max(1, std::min(kMaxGraphIters, o->graph_iters));
+  const bool timing = o->timing != 0;
+  while (timing && (int)c->tev.size() < 4 * G) {
+    cudaEvent_t e;
+    RSN_CUDA(c, cudaEventCreate(&e));
+    c->tev.push_back(e);
   }
-
-  auto body = [&](int iters) -> cudaError_t {
+  auto body = [&](int iters, bool capturing) -> cudaError_t {
+    // inside stream capture an event record must be an external node to be timeable
+    const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     for (int it = 0; it < iters; ++it) {
-      cudaError_t e = launch_op(OP_COCG, fp32, c->R, cfg.inner.ppt, gi, cfg.inner.threads, cfg.inner.smem, st, ji, b,
-                                nullptr, nullptr, nullptr);
+      cudaError_t e;
+      if ((e = launch_zero(fp32, S, nB, st, jr, bdev)) != cudaSuccess) return e;
+      if (proj && (e = launch_project(1, fp32, S, c->n_groups, st, jr, bdev, nullptr, w.c_x.p)) != cudaSuccess)
+        return e;
+      if ((e = launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, bdev,
+                         nullptr, nullptr, nullptr)) != cudaSuccess)
+        return e;
+      if ((e = launch_x_update(fp32, S, nB, st, jr, bdev)) != cudaSuccess) return e;
+      if ((e = launch_sched(S, it, st, jr, bdev)) != cudaSuccess) return e;
+      if ((e = launch_emit(S, st, jr, bdev)) != cudaSuccess) return e;
+      if (proj && (e = launch_project(0, fp32, S, c->n_groups, st, ji, bdev, nullptr, w.c_r.p)) != cudaSuccess)
+        return e;
+      if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it], st, evf)) != cudaSuccess) return e;
+      e = cfg.inner.tma ? launch_op_tma(OP_COCG, fp32, c->R, gi, cfg.inner.threads, cfg.inner.smem, st, ji, bdev,
+                                        nullptr, nullptr, nullptr)
+                        : launch_op(OP_COCG, fp32, c->R, cfg.inner.ppt, gi, cfg.inner.threads, cfg.inner.smem, st, ji,
+                                    bdev, nullptr, nullptr, nullptr);
       if (e != cudaSuccess) return e;
-      if ((e = launch_cocg_update(fp32, S, nB, st, ji, b)) != cudaSuccess) return e;
-      if (proj && (e = launch_project(0, fp32, S, c->n_groups, st, ji, b, nullptr, b.c_r)) != cudaSuccess) return e;
-      if ((e = launch_inner_book(S, o->max_iter, st, ji, b)) != cudaSuccess) return e;
+      if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 1], st, evf)) != cudaSuccess) return e;
+      if ((e = launch_cocg_update(fp32, S, nB, st, ji, bdev)) != cudaSuccess) return e;
+      if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 2], st, evf)) != cudaSuccess) return e;
+      if ((e = launch_book(S, it, st, ji, bdev)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
-  const int per_iter = proj ? 4 : 3;
-  const int G = std::max(1, o->graph_iters);
+  const int per_iter = proj ? 10 : 8;
+  const double vbytes = (double)N * (fp32 ? sizeof(float2) : sizeof(double2));
   cudaGraphExec_t gexec = nullptr;
   if (o->use_graph) {
-    GraphKey key{fp32 ? 1 : 0, S, G, w.generation, proj ? 1 : 0};
+    GraphKey key{fp32 ? 1 : 0, S, G, w.generation, proj ? 1 : 0, timing ? 1 : 0};
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
       gexec = it->second;
     } else {
       cudaGraph_t g = nullptr;
       RSN_CUDA(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = body(G);
+      cudaError_t e = body(G, true);
       cudaError_t e2 = cudaStreamEndCapture(st, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -763,75 +867,77 @@ static rsn_status run_batch(rsn_ctx* c, const rsn_solver_opts* o, int nact, cons
     }
   }
 
-  bool timeout = false;
-  for (int outer = 0; outer <= o->max_outer + 1; ++outer) {
-    if (proj) {
-      RSN_CUDA(c, launch_project(1, fp32, S, c->n_groups, st, jr, b, nullptr, b.c_x));
-      ++launches;
+  // every system needs at most max_iter COCG iterations plus one iteration per
+  // true residual; this bounds the replays even if the device state were wrong
+  const long long waves = (nsys + S - 1) / S;
+  const long long max_replays = (waves * ((long long)o->max_iter + 2LL * o->max_outer + 8) + G) / G + 4;
+  bool timeout = false, finished = false;
+  int* hs = c->sched_host;
+  for (long long rep = 0; rep < max_replays; ++rep) {
+    if (gexec) {
+      RSN_CUDA(c, cudaGraphLaunch(gexec, st));
+    } else {
+      RSN_CUDA(c, body(G, false));
     }
-    RSN_CUDA(c, launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, b,
-                          nullptr, nullptr, nullptr));
-    RSN_CUDA(c, launch_x_update(fp32, S, nB, st, jr, b));
-    RSN_CUDA(c, launch_outer_book(S, o->tol, o->tol_inner, o->max_outer, st, jr, b));
-    launches += 3;
-    RSN_CUDA(c, cudaMemcpyAsync(c->n_active_host, b.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    c->st_launches += (int64_t)G * per_iter;
+    RSN_CUDA(c, cudaMemcpyAsync(hs, w.sched.p, (3 + 2 * kMaxGraphIters) * sizeof(int), cudaMemcpyDeviceToHost, st));
     RSN_CUDA(c, cudaStreamSynchronize(st));
-    if (c->n_active_host[1] == 0) break;
-    c->st_sweeps++;
-    if (proj) {
-      RSN_CUDA(c, launch_project(0, fp32, S, c->n_groups, st, ji, b, nullptr, b.c_r));
-      ++launches;
-    }
-    // inner COCG: replay the captured iteration body until no system is active
-    for (int rep = 0;; ++rep) {
-      if (gexec) {
-        RSN_CUDA(c, cudaGraphLaunch(gexec, st));
-      } else {
-        RSN_CUDA(c, body(G));
+    if (timing) {
+      for (int it = 0; it < G; ++it) {
+        const int act = hs[3 + kMaxGraphIters + it];
+        float m0 = 0.f, m1 = 0.f;
+        RSN_CUDA(c, cudaEventElapsedTime(&m0, c->tev[4 * it], c->tev[4 * it + 1]));
+        RSN_CUDA(c, cudaEventElapsedTime(&m1, c->tev[4 * it + 1], c->tev[4 * it + 2]));
+        if (act == 0) continue;
+        c->ks_launches[0]++;
+        c->ks_launches[1]++;
+        c->ks_ms[0] += m0;
+        c->ks_ms[1] += m1;
+        c->ks_bytes[0] += 4.0 * vbytes * act;
+        c->ks_bytes[1] += 6.0 * vbytes * act;
       }
-      launches += (int64_t)G * per_iter;
-      RSN_CUDA(c, cudaMemcpyAsync(c->n_active_host, b.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-      RSN_CUDA(c, cudaStreamSynchronize(st));
-      if (c->n_active_host[0] == 0) break;
-      if (o->deadline_ms > 0) {
-        const double el_ms =
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-        if (el_ms > o->deadline_ms) {
-          timeout = true;
-          break;
-        }
-      }
-      if ((long long)rep * G > (long long)o->max_iter + G) break;  // safety: max_iter bounds every slot
     }
-    if (timeout) break;
+    if (hs[2] != 0) RSN_FAIL(c, RSN_ECUDA, "a bulk copy did not arrive within its bounded wait (kernel aborted)");
+    if (hs[0] >= nsys && hs[1] == 0) {
+      finished = true;
+      break;
+    }
+    if (o->deadline_ms > 0) {
+      const double el_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+      if (el_ms > o->deadline_ms) {
+        timeout = true;
+        break;
+      }
+    }
   }
-  c->st_launches += launches;
-  res.total_iters.resize(S);
-  res.status.resize(S);
-  res.outer_done.resize(S);
-  res.n_outer.resize(S);
-  res.relres.resize(S);
-  RSN_CUDA(c, cudaMemcpyAsync(res.total_iters.data(), w.total_iters.p, S * sizeof(int), cudaMemcpyDeviceToHost, st));
-  RSN_CUDA(c, cudaMemcpyAsync(res.status.data(), w.status.p, S * sizeof(int), cudaMemcpyDeviceToHost, st));
-  RSN_CUDA(c, cudaMemcpyAsync(res.outer_done.data(), w.outer_done.p, S * sizeof(int), cudaMemcpyDeviceToHost, st));
-  RSN_CUDA(c, cudaMemcpyAsync(res.n_outer.data(), w.n_outer.p, S * sizeof(int), cudaMemcpyDeviceToHost, st));
-  RSN_CUDA(c, cudaMemcpyAsync(res.relres.data(), w.relres.p, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (!finished && !timeout) RSN_FAIL(c, RSN_ECUDA, "streaming solver exceeded its iteration bound");
+  out.iters.resize(nsys);
+  out.status.resize(nsys);
+  out.relres.resize(nsys);
+  unsigned long long cnt[4] = {0, 0, 0, 0};
+  RSN_CUDA(c, cudaMemcpyAsync(out.iters.data(), q.out_iters.p, nsys * sizeof(int), cudaMemcpyDeviceToHost, st));
+  RSN_CUDA(c, cudaMemcpyAsync(out.status.data(), q.out_status.p, nsys * sizeof(int), cudaMemcpyDeviceToHost, st));
+  RSN_CUDA(c, cudaMemcpyAsync(out.relres.data(), q.out_relres.p, nsys * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RSN_CUDA(c, cudaMemcpyAsync(cnt, w.counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
   RSN_CUDA(c, cudaStreamSynchronize(st));
-  res.timeout = timeout;
+  out.timeout = timeout;
+  out.krylov = cnt[0];
+  out.updates = cnt[1];
+  c->st_iters += (int64_t)cnt[0];
+  c->st_sweeps += (int64_t)cnt[1];
   return RSN_OK;
 }
 
-// classify a finished batch into an overall status; fills iters/relres
-static rsn_status batch_status(const BatchResult& r, int nact, double tol, int32_t* iters, double* relres) {
+// classify finished systems into an overall status; fills iters/relres
+static rsn_status stream_status(const StreamOut& r, long long n0, long long n, int32_t* iters, double* relres) {
   rsn_status worst = RSN_OK;
-  for (int s = 0; s < nact; ++s) {
-    const bool ok = r.outer_done[s] && r.status[s] == 0 && r.relres[s] <= tol;
-    if (iters) iters[s] = ok ? r.total_iters[s] : -std::max(1, r.total_iters[s]);
-    if (relres) relres[s] = r.relres[s];
-    if (!ok) {
-      rsn_status e = r.timeout ? RSN_ETIMEOUT : (r.status[s] == 2 ? RSN_EBREAKDOWN : RSN_ENOCONV);
-      if (worst == RSN_OK) worst = e;
-    }
+  for (long long k = 0; k < n; ++k) {
+    const int stt = r.status[n0 + k];
+    const bool ok = stt == 0;
+    if (iters) iters[k] = ok ? r.iters[n0 + k] : -std::max(1, r.iters[n0 + k]);
+    if (relres) relres[k] = r.relres[n0 + k];
+    if (!ok && worst == RSN_OK)
+      worst = (stt < 0 || r.timeout) ? RSN_ETIMEOUT : (stt == 2 ? RSN_EBREAKDOWN : RSN_ENOCONV);
   }
   return worst;
 }
@@ -841,13 +947,20 @@ static rsn_status check_solve_args(rsn_ctx* c, int n_e, const double* E, int n_c
   if (n_e < 0 || n_cols < 0) RSN_FAIL(c, RSN_EINVAL, "negative sizes");
   if ((n_e > 0 && !E) || (n_cols > 0 && !cols) || !o) RSN_FAIL(c, RSN_EINVAL, "NULL argument");
   if (o->precision != RSN_FP64 && o->precision != RSN_MIXED) RSN_FAIL(c, RSN_EINVAL, "bad precision");
-  if (!(o->tol > 0) || !(o->tol_inner > 0) || o->max_iter < 1 || o->max_outer < 0)
+  if (!(o->tol > 0) || !(o->tol_inner > 0) || !(o->tol_inner < 1) || o->max_iter < 1 || o->max_outer < 1 ||
+      o->graph_iters < 0 || o->rhs_block < 0)
     RSN_FAIL(c, RSN_EINVAL, "bad solver options");
   for (int e = 0; e < n_e; ++e)
     if (!std::isfinite(E[e])) RSN_FAIL(c, RSN_EINVAL, "E[%d] is not finite", e);
   for (int k = 0; k < n_cols; ++k)
     if (cols[k] < 0 || cols[k] >= c->N) RSN_FAIL(c, RSN_EINVAL, "cols[%d] = %d out of range", k, cols[k]);
+  if ((long long)n_e * n_cols >= (1LL << 30)) RSN_FAIL(c, RSN_EINVAL, "too many systems in one call");
   return RSN_OK;
+}
+
+static void reset_stats(rsn_ctx* c) {
+  c->st_iters = c->st_sweeps = c->st_launches = 0;
+  for (int k = 0; k < 2; ++k) c->ks_launches[k] = 0, c->ks_ms[k] = 0, c->ks_bytes[k] = 0;
 }
 
 extern "C" {
@@ -861,24 +974,48 @@ rsn_status rsn_apply(rsn_ctx* c, int precision, int n_rhs, const double* E, cons
   if (n_rhs == 0) return RSN_OK;
   if ((rs = enter(c)) != RSN_OK) return rs;
   const bool fp32 = precision == RSN_MIXED;
-  if ((rs = ensure_ws(c, fp32, false, n_rhs, false)) != RSN_OK) return rs;
-  Workspace& w = c->ws;
-  std::vector<double> hE(E, E + n_rhs);
-  hE.resize(w.slots, 0.0);
-  std::vector<int> hj(w.slots, 0);
-  std::vector<long long> hvo(w.slots);
-  for (int s = 0; s < w.slots; ++s) hvo[s] = (long long)s * c->N;
-  RSN_CUDA(c, cudaMemcpyAsync(w.E.p, hE.data(), w.slots * sizeof(double), cudaMemcpyHostToDevice, c->st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.junc.p, hj.data(), w.slots * sizeof(int), cudaMemcpyHostToDevice, c->st));
-  RSN_CUDA(c, cudaMemcpyAsync(w.voff.p, hvo.data(), w.slots * sizeof(long long), cudaMemcpyHostToDevice, c->st));
-  LaunchCfg cfg;
-  if ((rs = make_cfg(c, fp32, w.slots, cfg)) != RSN_OK) return rs;
-  Tiling t = choose_tiling(c, !fp32, OP_APPLY, w.slots);
-  BatchDev b = batch_view(c, nullptr, nullptr);
+  CallBufs& q = c->cb;
+  // small per-call arrays: E, junction ids, offsets, projections
+  RSN_CUDA(c, q.sys_E.ensure(n_rhs * sizeof(double)));
+  RSN_CUDA(c, q.sys_junc.ensure(n_rhs * sizeof(int)));
+  RSN_CUDA(c, q.sys_xo.ensure(n_rhs * sizeof(long long)));
+  RSN_CUDA(c, q.out_t.ensure((size_t)n_rhs * std::max(1, c->n_proj) * sizeof(double2)));
+  RSN_CUDA(c, c->bd.ensure(2 * sizeof(BatchDev)));
+  std::vector<int> hj(n_rhs, 0);
+  std::vector<long long> hvo(n_rhs);
+  for (int s = 0; s < n_rhs; ++s) hvo[s] = (long long)s * c->N;
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_E.p, E, n_rhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_junc.p, hj.data(), n_rhs * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_xo.p, hvo.data(), n_rhs * sizeof(long long), cudaMemcpyHostToDevice, c->st));
+  BatchDev b;
+  memset(&b, 0, sizeof(b));
   b.nslots = n_rhs;
-  if (c->n_proj > 0) RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->st, cfg.jt_inner, b, x_dev, b.c_r));
-  RSN_CUDA(c, launch_op(OP_APPLY, fp32, c->R, t.ppt, dim3(cfg.inner.n, n_rhs), t.threads, t.smem, c->st,
-                        cfg.jt_inner, b, x_dev, y_dev, b.c_r));
+  b.junc = q.sys_junc.as<int>();
+  b.E = q.sys_E.as<double>();
+  b.voff = q.sys_xo.as<long long>();
+  RSN_CUDA(c, cudaMemcpyAsync(c->bd.as<BatchDev>() + 1, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));
+  const BatchDev* bdev = c->bd.as<BatchDev>() + 1;
+  LaunchCfg cfg;
+  if ((rs = make_cfg(c, fp32, n_rhs, cfg)) != RSN_OK) return rs;
+  const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs);
+  void* cbuf = q.out_t.p;
+  if (c->n_proj > 0)
+    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
+  const bool aligned = (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0;
+  if (t.tma && aligned) {
+    RSN_CUDA(c, launch_op_tma(OP_APPLY, fp32, c->R, dim3(cfg.inner.n, n_rhs), t.threads, t.smem, c->st,
+                              cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
+  } else {
+    const Tiling t2 = [&] {
+      Tiling u = t;
+      u.tma = false;
+      u.smem = op_smem_bytes(fp32, OP_APPLY, c->R, u.TY, c->nx, c->n_proj);
+      u.threads = ((c->nx * u.TY + u.ppt - 1) / u.ppt + 31) / 32 * 32;
+      return u;
+    }();
+    RSN_CUDA(c, launch_op(OP_APPLY, fp32, c->R, t2.ppt, dim3(cfg.inner.n, n_rhs), t2.threads, t2.smem, c->st,
+                          cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
+  }
   return leave(c);
 }
 
@@ -888,32 +1025,24 @@ rsn_status rsn_solve_columns(rsn_ctx* c, int n_e, const double* E, int n_cols, c
   rsn_status rs = commit_setup(c);
   if (rs != RSN_OK) return rs;
   if ((rs = check_solve_args(c, n_e, E, n_cols, cols, o)) != RSN_OK) return rs;
-  const long long total = (long long)n_e * n_cols;
-  if (total == 0) return RSN_OK;
+  const long long nsys = (long long)n_e * n_cols;
+  if (nsys == 0) return RSN_OK;
   if (!x_dev) RSN_FAIL(c, RSN_EINVAL, "x_dev is NULL");
   if ((rs = enter(c)) != RSN_OK) return rs;
-  const bool fp32 = o->precision == RSN_MIXED;
-  const int S = choose_slots(c, o, false, total);
-  if ((rs = ensure_ws(c, fp32, false, S, false)) != RSN_OK) return rs;
-  c->st_iters = c->st_sweeps = c->st_launches = 0;
+  reset_stats(c);
   const auto t_start = std::chrono::steady_clock::now();
   RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
-  rsn_status worst = RSN_OK;
-  std::vector<double> bE(S);
-  std::vector<int> bc(S);
-  for (long long s0 = 0; s0 < total; s0 += S) {
-    const int nact = (int)std::min<long long>(S, total - s0);
-    for (int s = 0; s < nact; ++s) {
-      bE[s] = E[(s0 + s) / n_cols];
-      bc[s] = cols[(s0 + s) % n_cols];
-    }
-    double2* x64 = reinterpret_cast<double2*>(x_dev) + s0 * c->N;
-    BatchResult br;
-    if ((rs = run_batch(c, o, nact, bE.data(), bc.data(), x64, nullptr, t_start, br)) != RSN_OK) return rs;
-    for (int s = 0; s < nact; ++s) c->st_iters += br.total_iters[s];
-    rsn_status bs = batch_status(br, nact, o->tol, iters ? iters + s0 : nullptr, relres ? relres + s0 : nullptr);
-    if (worst == RSN_OK) worst = bs;
+  StreamIn in;
+  in.resize(nsys);
+  for (long long k = 0; k < nsys; ++k) {
+    in.E[k] = E[k / n_cols];
+    in.col[k] = cols[k % n_cols];
+    in.xo[k] = k * c->N;
   }
+  StreamOut so;
+  if ((rs = run_stream(c, o, in, reinterpret_cast<double2*>(x_dev), nullptr, false, 0, t_start, so)) != RSN_OK)
+    return rs;
+  const rsn_status worst = stream_status(so, 0, nsys, iters, relres);
   RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
   RSN_CUDA(c, cudaEventSynchronize(c->t1));
   float ms = 0;
@@ -934,75 +1063,78 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
   const bool adjoint = dV != nullptr;
   if (adjoint && n_e > 0 && !T_bar) RSN_FAIL(c, RSN_EINVAL, "T_bar is NULL");
   if ((rs = enter(c)) != RSN_OK) return rs;
-  const long long total = (long long)n_e * n_cols;
-  const bool fp32 = o->precision == RSN_MIXED;
-  c->st_iters = c->st_sweeps = c->st_launches = 0;
-  DevBuf t_all, gr_cols, Td, g, oi;
-  RSN_CUDA(c, t_all.ensure(std::max<long long>(1, total) * sizeof(double)));
-  RSN_CUDA(c, gr_cols.ensure(std::max(1, n_cols) * sizeof(double)));
-  RSN_CUDA(c, Td.ensure(std::max(1, n_e) * sizeof(double)));
+  reset_stats(c);
+  CallBufs& q = c->cb;
+  const long long N = c->N;
+  RSN_CUDA(c, q.gr_cols.ensure(std::max(1, n_cols) * sizeof(double)));
+  RSN_CUDA(c, q.Td.ensure(std::max(1, n_e) * sizeof(double)));
   if (adjoint) {
-    RSN_CUDA(c, g.ensure(c->N * sizeof(double)));
-    RSN_CUDA(c, cudaMemsetAsync(g.p, 0, c->N * sizeof(double), c->st));
+    RSN_CUDA(c, q.g.ensure(N * sizeof(double)));
+    RSN_CUDA(c, cudaMemsetAsync(q.g.p, 0, N * sizeof(double), c->st));
   }
   std::vector<double> hgr(std::max(1, n_cols));
   for (int k = 0; k < n_cols; ++k) hgr[k] = c->gr[cols[k]];
-  RSN_CUDA(c, cudaMemcpyAsync(gr_cols.p, hgr.data(), hgr.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.gr_cols.p, hgr.data(), hgr.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
   const auto t_start = std::chrono::steady_clock::now();
   RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
   rsn_status worst = RSN_OK;
-  if (total > 0) {
-    const int S = choose_slots(c, o, adjoint, total);
-    if ((rs = ensure_ws(c, fp32, adjoint, S, true)) != RSN_OK) return rs;
-    Workspace& w = c->ws;
-    std::vector<double> bE(S), hw(S);
-    std::vector<int> bc(S), hoi(S), bcadj(S, -1);
-    for (long long s0 = 0; s0 < total; s0 += S) {
-      const int nact = (int)std::min<long long>(S, total - s0);
-      for (int s = 0; s < S; ++s) {
-        if (s < nact) {
-          bE[s] = E[(s0 + s) / n_cols];
-          bc[s] = cols[(s0 + s) % n_cols];
-          hoi[s] = (int)(s0 + s);
-          hw[s] = adjoint ? 8.0 * c->gr[bc[s]] * T_bar[(s0 + s) / n_cols] : 0.0;
-        } else {
-          hoi[s] = -1;
-          hw[s] = 0.0;
-        }
-      }
-      BatchResult br;
-      double2* X0 = w.X0.as<double2>();
-      if ((rs = run_batch(c, o, nact, bE.data(), bc.data(), X0, nullptr, t_start, br)) != RSN_OK) return rs;
-      for (int s = 0; s < nact; ++s) c->st_iters += br.total_iters[s];
-      rsn_status bs = batch_status(br, nact, o->tol, nullptr, nullptr);
-      if (worst == RSN_OK) worst = bs;
-      RSN_CUDA(c, cudaMemcpyAsync(w.out_index.p, hoi.data(), S * sizeof(int), cudaMemcpyHostToDevice, c->st));
-      BatchDev bv = batch_view(c, X0, nullptr);
-      LaunchCfg cfg;
-      if ((rs = make_cfg(c, fp32, S, cfg)) != RSN_OK) return rs;
-      RSN_CUDA(c, launch_t_partial(S, c->st, cfg.jt_inner, bv, w.out_index.as<int>(), t_all.as<double>()));
-      c->st_launches += 1;
+  // energies per chunk: the adjoint keeps the forward and adjoint solutions of a
+  // chunk (2 * chunk * n_cols * N complex128) resident
+  int chunk = n_e;
+  if (adjoint && n_cols > 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const double per_e = 2.0 * n_cols * (double)N * sizeof(double2);
+    chunk = (int)std::max(1.0, std::min((double)n_e, 0.45 * (double)fr / per_e));
+  }
+  for (int e0 = 0; e0 < n_e && n_cols > 0; e0 += chunk) {
+    const int ne = std::min(chunk, n_e - e0);
+    const long long M = (long long)ne * n_cols;
+    StreamIn in;
+    in.resize(adjoint ? 2 * M : M);
+    for (long long k = 0; k < M; ++k) {
+      in.E[k] = E[e0 + k / n_cols];
+      in.col[k] = cols[k % n_cols];
+      in.xo[k] = adjoint ? k * N : -1;
       if (adjoint) {
-        BatchResult ba;
-        double2* X1 = w.X1.as<double2>();
-        if ((rs = run_batch(c, o, nact, bE.data(), bcadj.data(), X1, X0, t_start, ba)) != RSN_OK) return rs;
-        for (int s = 0; s < nact; ++s) c->st_iters += ba.total_iters[s];
-        bs = batch_status(ba, nact, o->tol, nullptr, nullptr);
-        if (worst == RSN_OK) worst = bs;
-        RSN_CUDA(c, cudaMemcpyAsync(w.wt.p, hw.data(), S * sizeof(double), cudaMemcpyHostToDevice, c->st));
-        BatchDev ba_v = batch_view(c, X1, X0);
-        RSN_CUDA(c, launch_grad_accum(S, c->N, c->st, ba_v, w.wt.as<double>(), g.as<double>()));
-        c->st_launches += 1;
+        in.E[M + k] = in.E[k];
+        in.col[M + k] = -1;
+        in.xo[M + k] = (M + k) * N;
+        in.xfo[M + k] = k * N;
+        in.dep[M + k] = (int)k;
       }
     }
+    double2* X = nullptr;
+    size_t reserved = 0;
+    if (adjoint) {
+      RSN_CUDA(c, q.X0.ensure((size_t)(2 * M) * N * sizeof(double2)));
+      X = q.X0.as<double2>();
+    }
+    StreamOut so;
+    if ((rs = run_stream(c, o, in, X, X, true, reserved, t_start, so)) != RSN_OK) return rs;
+    rsn_status bs = stream_status(so, 0, (long long)in.E.size(), nullptr, nullptr);
+    if (worst == RSN_OK) worst = bs;
+    RSN_CUDA(c, launch_t_final(ne, n_cols, c->st, q.out_t.as<double>(), q.gr_cols.as<double>(),
+                               q.Td.as<double>() + e0));
+    c->st_launches += 1;
+    if (adjoint) {
+      std::vector<double> hw(M);
+      for (long long k = 0; k < M; ++k) hw[k] = 8.0 * c->gr[in.col[k]] * T_bar[e0 + k / n_cols];
+      RSN_CUDA(c, q.wt.ensure(M * sizeof(double)));
+      RSN_CUDA(c, cudaMemcpyAsync(q.wt.p, hw.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      RSN_CUDA(c, launch_grad_sys((int)M, N, c->st, X + M * N, X, q.wt.as<double>(), q.g.as<double>()));
+      c->st_launches += 1;
+      RSN_CUDA(c, cudaStreamSynchronize(c->st));  // hw lives on the host stack
+    }
   }
-  RSN_CUDA(c, launch_t_final(n_e, n_cols, c->st, t_all.as<double>(), gr_cols.as<double>(), Td.as<double>()));
-  c->st_launches += 1;
   RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
-  if (T && n_e > 0) RSN_CUDA(c, cudaMemcpyAsync(T, Td.p, n_e * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if (T && n_e > 0) {
+    if (n_cols == 0) RSN_CUDA(c, cudaMemsetAsync(q.Td.p, 0, n_e * sizeof(double), c->st));
+    RSN_CUDA(c, cudaMemcpyAsync(T, q.Td.p, n_e * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  }
   if (adjoint) {
-    RSN_CUDA(c, cudaMemcpyAsync(dV, g.p, c->N * sizeof(double),
-                                dV_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+    RSN_CUDA(c, cudaMemcpyAsync(dV, q.g.p, N * sizeof(double), dV_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->st));
   }
   RSN_CUDA(c, cudaStreamSynchronize(c->st));
   float ms = 0;
@@ -1028,6 +1160,148 @@ rsn_status rsn_transmission_vjp(rsn_ctx* c, int n_e, const double* E, int n_cols
   return transmission_impl(c, n_e, E, n_cols, cols, o, T_bar, dV, dV_is_device, T);
 }
 
+// One kernel of the COCG iteration in isolation: every slot ACTIVE with a
+// synthetic, finite state; `reps` back-to-back launches timed with CUDA events.
+static rsn_status bench_kernel_impl(rsn_ctx* c, int precision, int kind, int S, int reps, double* ms_out,
+                                    double* bytes_out) {
+  const bool fp32 = precision == RSN_MIXED;
+  rsn_status rs = ensure_ws(c, fp32, S);
+  if (rs != RSN_OK) return rs;
+  Workspace& w = c->ws;
+  cudaStream_t st = c->st;
+  const long long N = c->N;
+  const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
+  const size_t vb = (size_t)S * N;
+  for (DevBuf* v : {&w.r, &w.p0, &w.p1, &w.q, &w.d}) RSN_CUDA(c, cudaMemsetAsync(v->p, 0x3c, vb * el, st));
+  RSN_CUDA(c, cudaMemsetAsync(w.Xslot.p, 0x3c, vb * sizeof(double2), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.rho.p, 0x3f, (size_t)S * w.PB * sizeof(double2), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.rho_cur.p, 0x3f, S * sizeof(double2), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.beta_cur.p, 0x3f, S * sizeof(double2), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.nrm.p, 0x3f, (size_t)S * w.PB * sizeof(double), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.mu.p, 0x3f, (size_t)S * w.PA * sizeof(double2), st));
+  const size_t npj = std::max(1, c->n_proj);
+  RSN_CUDA(c, cudaMemsetAsync(w.c_r.p, 0, (size_t)S * npj * sizeof(double2), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.c_p.p, 0, 2 * (size_t)S * npj * sizeof(double2), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.c_x.p, 0, (size_t)S * npj * sizeof(double2), st));
+  std::vector<int> hstate(S, kind == 2 ? SL_CHECK : SL_ACTIVE), hone(S, 1), hzero(S, 0), hcol(S, 0);
+  std::vector<double> hE(S, 0.2);
+  std::vector<long long> hvo(S);
+  for (int s = 0; s < S; ++s) hvo[s] = (long long)s * N;
+  RSN_CUDA(c, cudaMemcpyAsync(w.state.p, hstate.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(w.iters.p, hone.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(w.junc.p, hzero.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(w.col.p, hcol.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(w.E.p, hE.data(), S * sizeof(double), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(w.xo.p, hvo.data(), S * sizeof(long long), cudaMemcpyHostToDevice, st));
+  rsn_solver_opts o;
+  rsn_default_opts(precision, &o);
+  BatchDev b = slot_batch(c, S, &o);
+  RSN_CUDA(c, cudaMemcpyAsync(c->bd.p, &b, sizeof(b), cudaMemcpyHostToDevice, st));
+  const BatchDev* bdev = c->bd.as<BatchDev>();
+  LaunchCfg cfg;
+  if ((rs = make_cfg(c, fp32, S, cfg)) != RSN_OK) return rs;
+  auto launch = [&]() -> cudaError_t {
+    if (kind == 0)
+      return cfg.inner.tma ? launch_op_tma(OP_COCG, fp32, c->R, dim3(cfg.inner.n, S), cfg.inner.threads,
+                                           cfg.inner.smem, st, cfg.jt_inner, bdev, nullptr, nullptr, nullptr)
+                           : launch_op(OP_COCG, fp32, c->R, cfg.inner.ppt, dim3(cfg.inner.n, S), cfg.inner.threads,
+                                       cfg.inner.smem, st, cfg.jt_inner, bdev, nullptr, nullptr, nullptr);
+    if (kind == 1) return launch_cocg_update(fp32, S, c->jh.nB, st, cfg.jt_inner, bdev);
+    return launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, dim3(cfg.resid.n, S), cfg.resid.threads, cfg.resid.smem,
+                     st, cfg.jt_resid, bdev, nullptr, nullptr, nullptr);
+  };
+  for (int i = 0; i < 2; ++i) RSN_CUDA(c, launch());
+  RSN_CUDA(c, cudaEventRecord(c->t0, st));
+  for (int i = 0; i < reps; ++i) RSN_CUDA(c, launch());
+  RSN_CUDA(c, cudaEventRecord(c->t1, st));
+  RSN_CUDA(c, cudaEventSynchronize(c->t1));
+  float ms = 0.f;
+  RSN_CUDA(c, cudaEventElapsedTime(&ms, c->t0, c->t1));
+  if (ms_out) *ms_out = ms / reps;
+  const double v = (double)N * S;
+  if (bytes_out)
+    *bytes_out = kind == 0 ? 4.0 * el * v : kind == 1 ? 6.0 * el * v : (sizeof(double2) + 2.0 * el) * v;
+  return RSN_OK;
+}
+
+rsn_status rsn_bench_kernel(rsn_ctx* c, int precision, int kind, int nslots, int reps, double* ms_per_launch,
+                            double* bytes_per_launch) {
+  if (!c) return RSN_EINVAL;
+  rsn_status rs = commit_setup(c);
+  if (rs != RSN_OK) return rs;
+  if ((precision != RSN_FP64 && precision != RSN_MIXED) || kind < 0 || kind > 2 || nslots < 1 || reps < 1)
+    RSN_FAIL(c, RSN_EINVAL, "bad benchmark arguments");
+  if ((rs = enter(c)) != RSN_OK) return rs;
+  if ((rs = bench_kernel_impl(c, precision, kind, nslots, reps, ms_per_launch, bytes_per_launch)) != RSN_OK)
+    return rs;
+  return leave(c);
+}
+
+// Search the operator kernel's tiling for this grid, precision and slot count:
+// plane-streaming kernel with several z-chunk lengths, and the register-prefetch
+// kernel over (TY, ppt, Lz).  The fastest is kept as the context's tiling.
+rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz, int* ppt, int* tma,
+                        double* best_gbs) {
+  if (!c) return RSN_EINVAL;
+  rsn_status rs = commit_setup(c);
+  if (rs != RSN_OK) return rs;
+  if ((precision != RSN_FP64 && precision != RSN_MIXED) || nslots < 1) RSN_FAIL(c, RSN_EINVAL, "bad arguments");
+  if ((rs = enter(c)) != RSN_OK) return rs;
+  const bool fp32 = precision == RSN_MIXED;
+  struct Cand { int TY, Lz, ppt, notma; };
+  std::vector<Cand> cands;
+  std::vector<int> lzs;
+  for (int zt : {1, 2, 3, 4, 6, 8}) {
+    const int lz = (c->nz + zt - 1) / zt;
+    if (lz >= 2 * c->R + 2 || zt == 1) lzs.push_back(lz);
+  }
+  for (int lz : lzs) cands.push_back({0, lz, 0, 0});
+  for (int p = 1; p <= 4; ++p)
+    for (int ty : {c->ny, (c->ny + 1) / 2, (c->ny + 2) / 3})
+      for (int lz : lzs) {
+        const int thr = (c->nx * ty + p - 1) / p;
+        if (thr < 32 || thr > 512) continue;
+        cands.push_back({ty, lz, p, 1});
+      }
+  const int save[4] = {c->tile_override[0], c->tile_override[1], c->tile_override[2], c->tile_override[3]};
+  double best = -1.0;
+  Cand bestc = {0, 0, 0, 0};
+  for (const Cand& k : cands) {
+    c->tile_override[0] = k.TY;
+    c->tile_override[1] = k.Lz;
+    c->tile_override[2] = k.ppt;
+    c->tile_override[3] = k.notma;
+    c->ws.slots = 0;
+    double ms = 0, by = 0;
+    rs = bench_kernel_impl(c, precision, 0, nslots, 5, &ms, &by);
+    if (rs != RSN_OK) continue;  // e.g. a shared-memory size this tile cannot have
+    const double gbs = by / (ms * 1e6);
+    if (gbs > best) {
+      best = gbs;
+      bestc = k;
+    }
+  }
+  if (best < 0) {
+    for (int i = 0; i < 4; ++i) c->tile_override[i] = save[i];
+    RSN_FAIL(c, RSN_ECUDA, "no tiling candidate ran");
+  }
+  c->tile_override[0] = bestc.TY;
+  c->tile_override[1] = bestc.Lz;
+  c->tile_override[2] = bestc.ppt;
+  c->tile_override[3] = bestc.notma;
+  c->ws.slots = 0;
+  clear_graphs(c);
+  c->ws.generation++;
+  c->err.clear();
+  if (TY) *TY = bestc.TY;
+  if (Lz) *Lz = bestc.Lz;
+  if (ppt) *ppt = bestc.ppt;
+  if (tma) *tma = bestc.notma ? 0 : 1;
+  if (best_gbs) *best_gbs = best;
+  (void)fp32;
+  return leave(c);
+}
+
 // Tiling override used by the autotuner and the tests: TY, Lz, ppt (0 = auto).
 rsn_status rsn_set_tiling(rsn_ctx* c, int TY, int Lz, int ppt) {
   if (!c) return RSN_EINVAL;
@@ -1035,6 +1309,7 @@ rsn_status rsn_set_tiling(rsn_ctx* c, int TY, int Lz, int ppt) {
   c->tile_override[0] = TY;
   c->tile_override[1] = Lz;
   c->tile_override[2] = ppt;
+  c->tile_override[3] = 0;
   clear_graphs(c);
   c->ws.generation++;
   c->ws.slots = 0;  // partial strides may change

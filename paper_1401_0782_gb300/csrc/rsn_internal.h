@@ -1,12 +1,15 @@
 // Internal structures shared by the library's translation units.
 //
 // Data layout in device memory (per junction, N = nx*ny*nz points, x fastest):
-//   dg64/dg32   (N)  complex diagonal without E: (-V_loc + 3 c_0/(2h^2), Gamma_L+Gamma_R)
+//   dg64        (N)  complex diagonal without E: (-V_loc + 3 c_0/(2h^2), Gamma_L+Gamma_R)
+//   dg32        (N)  (-V_loc, Gamma_L+Gamma_R) for the FP32 difference-form stencil
 //   gl          (N)  Gamma_L (FP64), used by T and the adjoint right-hand side
 //   inv_*            per-point list of (projector, value) for the matvec epilogue
 //   grp_*            per-atom support lists for the projections c_p = v_p . x
-// Krylov vectors of one batch are stored column-contiguous: slot s owns
-// elements [voff[s], voff[s] + N) of every vector array.
+// Krylov vectors (r, p0, p1, q, d) are stored per slot: slot s owns elements
+// [voff[s], voff[s] + N) of each array.  The FP64 iterate of the system held by
+// slot s lives at x64[xo[s] ...], the forward solution an adjoint system reads at
+// xf[xfo[s] ...].
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -16,8 +19,10 @@ namespace rsn {
 constexpr int kMaxR = 6;        // up to the order-12 stencil
 constexpr int kMaxPlane = 4096; // nx*ny limit (smem plane tiles)
 constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
+constexpr int kMaxGraphIters = 256;
+constexpr int kSchedThreads = 1024;
 constexpr int kVecThreads = 256;
-constexpr int kVecPerThread = 8;   // points per thread in the streaming kernels
+constexpr int kVecPerThread = 16;  // points per thread in the streaming kernels
 constexpr int kVecPts = kVecThreads * kVecPerThread;
 
 struct JuncDev {
@@ -51,14 +56,40 @@ struct JuncDev {
   const double* ekb;
 };
 
-// Per-slot state of a batch of systems A(E_s) x_s = b_s.
+// Life cycle of a slot of the streaming solver.
+enum SlotState {
+  SL_FREE = 0,    // no system; gets the next one from the queue
+  SL_NEW = 1,     // system assigned: zero x and d, then true residual r = b
+  SL_CHECK = 2,   // recurrence reached its target: FP64 true residual + reliable update
+  SL_ACTIVE = 3,  // COCG iterations in the inner precision
+  SL_DRAIN = 4    // finished this iteration: outputs are emitted, then FREE
+};
+
+// Batch state.  Lives in device memory; kernels receive a pointer to it so
+// captured CUDA graphs stay valid when a call changes the buffers it points to.
 struct BatchDev {
   int nslots;
-  int PA, PB;  // partial-sum strides per slot (>= nA, nB of every junction)
-  const int* junc;
-  const double* E;
-  const int* col;          // >= 0: b = e_col ; -1: adjoint b = Gamma_L o conj(xf)
-  const long long* voff;
+  int PA, PB;  // partial-sum strides per slot (>= nA / nR and nB of every junction)
+  // per slot
+  int* state;
+  int* sys;
+  int* junc;
+  double* E;
+  int* col;             // >= 0: b = e_col ; -1: adjoint b = Gamma_L o conj(xf)
+  long long* voff;      // inner vectors
+  long long* xo;        // FP64 iterate
+  long long* xfo;       // forward solution (adjoint right-hand side)
+  int* iters;           // COCG iterations since the last restart (p = r at iters == 0)
+  int* total_iters;
+  int* cyc_iters;       // COCG iterations since the last true residual
+  int* n_upd;           // reliable updates so far
+  int* restart;         // breakdown seen: restart with p = r at the next update
+  double2* rho_cur;     // rho_k = r^T r of the current iteration (set by book / sched)
+  double2* beta_cur;    // beta_k = rho_k / rho_{k-1} for the direction update of iteration k
+  double* bnorm2;
+  double* rlast2;       // true ||r||^2 at the previous replacement (progress check)
+  double* tol2;         // recurrence target ||r||^2 of the current cycle
+  // vectors
   double2* x64;
   const double2* xf;
   void* r;
@@ -66,59 +97,62 @@ struct BatchDev {
   void* p1;
   void* q;
   void* d;
-  int* iters;       // Krylov iterations since the last restart
-  int* done;        // inner solve finished (or slot idle)
-  int* outer_done;  // slot finished for good
-  int* total_iters;
-  int* n_outer;
-  int* status;      // 0 ok, 1 no-conv, 2 breakdown seen
-  int* breakdowns;
-  double* bnorm2;
-  double* tol2;
-  double* relres;
-  double2* rho0_part;  // [nslots][PA] rho_0 from the true-residual kernel
-  double* nrm0_part;   // [nslots][PA]
-  double2* rho_part;   // [2][nslots][PB]
-  double* nrm_part;    // [nslots][PB]
-  double2* mu_part;    // [nslots][PA]
-  void* c_r;           // [nslots][n_proj] projections of r (inner precision)
-  void* c_p;           // [2][nslots][n_proj] projections of p
-  double2* c_x;        // [nslots][n_proj] projections of x64 + d (FP64)
-  int* n_active;       // [2]: inner active count, outer active count
+  // reduction partials
+  double2* rho0_part;   // [S][PA] true-residual kernel: r^T r
+  double* nrm0_part;    // [S][PA] true-residual kernel: ||r||^2
+  double2* rho_part;    // [S][PB] COCG update kernel: r^T r
+  double* nrm_part;     // [S][PB]
+  double2* mu_part;     // [S][PA] operator kernel: p^T A p
+  void* c_r;            // [S][n_proj] projections of r (inner precision)
+  void* c_p;            // [2][S][n_proj] projections of p
+  double2* c_x;         // [S][n_proj] projections of x64 + d (FP64)
+  // systems queue and outputs
+  int nsys;
+  const int* sys_junc;
+  const double* sys_E;
+  const int* sys_col;
+  const long long* sys_xo;   // x64 offset of each system (-1: slot storage)
+  const long long* sys_xfo;
+  const int* sys_dep;        // system that must finish first (adjoint after forward), -1 none
+  int* out_iters;
+  double* out_relres;
+  int* out_status;           // -1 pending, 0 converged, 1 not converged, 2 breakdown
+  double* out_t;             // T partial sum_{i in L} Gamma_L |x(i)|^2 per system (may be null)
+  int* sched;                // [0] next system, [1] busy slots, [3 + it] busy after iteration it of a
+                             // replay, [3 + kMaxGraphIters + it] systems that did a COCG iteration
+  unsigned long long* counters;  // [0] COCG iterations, [1] reliable updates
+  // options
+  double tol, delta;
+  int max_iter, max_upd;
+  int cycle_cap;  // a cycle longer than this ends with a true residual even if its target was not met
 };
 
 enum OpMode { OP_COCG = 0, OP_RESID = 1, OP_APPLY = 2 };
 
-struct OpLaunch {
-  int threads;  // CTA size
-  int ppt;      // owned points per thread
-  size_t smem;  // dynamic shared memory bytes
-};
-
 // ---- launchers (defined in the .cu files) --------------------------------
-// operator kernels (ops_r<R>.cu)
 cudaError_t launch_op(int mode, bool fp32, int R, int ppt, dim3 grid, int threads, size_t smem,
-                      cudaStream_t st, const JuncDev* jt, const BatchDev& b, const void* x_in,
+                      cudaStream_t st, const JuncDev* jt, const BatchDev* b, const void* x_in,
                       void* y_out, const void* c_in);
 size_t op_smem_bytes(bool fp32, int mode, int R, int TY, int nx, int n_proj);
+// plane-streaming (TMA) operator kernel for whole-plane tiles (OP_COCG / OP_APPLY)
+cudaError_t launch_op_tma(int mode, bool fp32, int R, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                          const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out, const void* c_in);
+size_t op_tma_smem_bytes(bool fp32, int mode, int R, int nx, int ny, int n_proj);
 
-// streaming / reduction kernels (vec_kernels.cu)
+cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
-                               const BatchDev& b);
+                               const BatchDev* b);
 cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, cudaStream_t st,
-                           const JuncDev* jt, const BatchDev& b, const void* x_in, void* c_out);
-cudaError_t launch_inner_book(int nslots, int max_iter, cudaStream_t st, const JuncDev* jt,
-                              const BatchDev& b);
-cudaError_t launch_outer_book(int nslots, double tol, double tol_inner, int max_outer,
-                              cudaStream_t st, const JuncDev* jt, const BatchDev& b);
+                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out);
+cudaError_t launch_book(int nslots, int slot_it, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
+constexpr int kBookWarps = 8;  // slots per CTA of the bookkeeping kernel (one warp each)
+cudaError_t launch_sched(int nslots, int slot_it, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
-                            const BatchDev& b);
-cudaError_t launch_bnorm_adjoint(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev& b);
-cudaError_t launch_t_partial(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev& b,
-                             const int* out_index, double* t_out);
+                            const BatchDev* b);
+cudaError_t launch_emit(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_t_final(int n_e, int n_cols, cudaStream_t st, const double* t_all,
                            const double* gr_cols, double* T_out);
-cudaError_t launch_grad_accum(int nslots, long long N, cudaStream_t st, const BatchDev& b,
-                              const double* wt, double* g);
+cudaError_t launch_grad_sys(int nsys, long long N, cudaStream_t st, const double2* lam, const double2* x,
+                            const double* wt, double* g);
 
 }  // namespace rsn

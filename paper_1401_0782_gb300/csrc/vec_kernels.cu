@@ -1,5 +1,18 @@
-// Streaming and reduction kernels of the batched COCG solve, the T(E)
-// reduction (Eq. T-realspace) and the adjoint gradient.
+// Streaming, reduction and scheduling kernels of the batched COCG solver,
+// the T(E) reduction (Eq. T-realspace) and the adjoint gradient.
+//
+// Per iteration of the streaming solver (all kernels skip slots in other states):
+//   zero      (NEW)            x = 0, d = 0
+//   project   (NEW|CHECK)      c_x = v_p . (x + d)                       [projectors]
+//   op RESID  (NEW|CHECK)      r = b - A (x + d) in FP64, ||r||^2, r^T r
+//   x_update  (NEW|CHECK)      x += d, d = 0
+//   sched     (all, 1 CTA)     converged? -> DRAIN; else reliable update -> ACTIVE;
+//                              DRAIN -> FREE; FREE slots take queued systems
+//   emit      (DRAIN)          T partial of the finished system
+//   project   (ACTIVE)         c_r = v_p . r                             [projectors]
+//   op COCG   (ACTIVE)         p = r + beta p, q = A p, p^T q
+//   update    (ACTIVE)         alpha = rho/mu, r -= alpha q, d += alpha p, r^T r, ||r||^2
+//   book      (ACTIVE, 1 CTA)  iteration counts; recurrence target reached -> CHECK
 #include <type_traits>
 
 #include "cplx.cuh"
@@ -9,29 +22,59 @@
 namespace rsn {
 
 // ---------------------------------------------------------------------------
+// zero x and d of newly assigned systems
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) zero_kernel(const JuncDev* __restrict__ jt,
+                                                           const BatchDev* __restrict__ bp) {
+  using C = typename cx<T>::t;
+  const BatchDev& b = *bp;
+  const int s = blockIdx.y;
+  if (b.state[s] != SL_NEW) return;
+  const JuncDev& J = jt[b.junc[s]];
+  if ((int)blockIdx.x >= J.nB) return;
+  const long long vo = b.voff[s], xo = b.xo[s];
+  const long long i0 = (long long)blockIdx.x * kVecPts, i1 = min(i0 + (long long)kVecPts, J.N);
+  C* dv = reinterpret_cast<C*>(b.d);
+  for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
+    b.x64[xo + i] = make_double2(0.0, 0.0);
+    dv[vo + i] = czero<C>();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // COCG update (after the operator kernel of the same iteration):
-//   alpha = rho_k / mu_k,  r -= alpha q,  d += alpha p_new   (d = alpha p at k = 0)
+//   alpha = rho_k / mu_k,  r -= alpha q,  d += alpha p_new,
 //   partial sums of rho_{k+1} = r^T r and ||r||^2.
 // Each CTA covers kVecPts consecutive points of one system.  A non-finite
 // alpha leaves r and d untouched and flags the slot through a NaN norm.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev* __restrict__ jt,
-                                                                  const BatchDev b) {
+                                                                  const BatchDev* __restrict__ bp) {
   using C = typename cx<T>::t;
+  const BatchDev& b = *bp;
   const int s = blockIdx.y;
-  if (b.done[s]) return;
+  if (b.state[s] != SL_ACTIVE) return;
   const JuncDev& J = jt[b.junc[s]];
   if ((int)blockIdx.x >= J.nB) return;
   __shared__ double red[32 * 3];
+  __shared__ double2 s_mu[64];
+  __shared__ double2 s_alpha;
   const int k = b.iters[s];
-  double2 mu = make_double2(0.0, 0.0);
-  {
-    const double2* mp = b.mu_part + (size_t)s * b.PA;
-    for (int t = 0; t < J.nA; ++t) { mu.x += mp[t].x; mu.y += mp[t].y; }
+  // mu = p^T A p from the operator kernel's partials: loaded in parallel,
+  // summed in a fixed order
+  const int nA = J.nA;
+  for (int t = threadIdx.x; t < nA; t += blockDim.x) s_mu[t & 63] = b.mu_part[(size_t)s * b.PA + t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 mu = make_double2(0.0, 0.0);
+    for (int t = 0; t < nA && t < 64; ++t) { mu.x += s_mu[t].x; mu.y += s_mu[t].y; }
+    s_alpha = cdiv(b.rho_cur[s], mu);
   }
-  const double2 a64 = cdiv(slot_rho(b, J, s, k), mu);
-  const size_t slot_out = ((size_t)((k + 1) & 1) * b.nslots + s) * b.PB + blockIdx.x;
+  __syncthreads();
+  const double2 a64 = s_alpha;
+  const size_t slot_out = (size_t)s * b.PB + blockIdx.x;
   if (!isfinite(a64.x) || !isfinite(a64.y)) {
     if (threadIdx.x == 0) {
       b.nrm_part[(size_t)s * b.PB + blockIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
@@ -55,7 +98,7 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
     C r = rv[g];
     r.x -= alpha.x * q.x - alpha.y * q.y;
     r.y -= alpha.x * q.y + alpha.y * q.x;
-    C d = (k == 0) ? czero<C>() : dv[g];
+    C d = dv[g];
     d = cfma(alpha, p, d);
     rv[g] = r;
     dv[g] = d;
@@ -73,24 +116,28 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
 }
 
 // ---------------------------------------------------------------------------
-// Projections c_p = v_p . v for every projector, one CTA per (atom, system):
+// Projections c_p = v_p . v for every projector, one CTA per (atom, slot):
 // the atom's support is gathered once and dotted with each of its projectors.
-//   PJ_R: v = r (inner precision)           -> c_r   (skip finished inner solves)
-//   PJ_X: v = x64 + d (FP64)                -> c_x   (skip finished systems)
-//   PJ_IN: v = x_in (apply entry point)     -> c_out
+//   PJ_R: v = r (inner precision), ACTIVE slots         -> c_r
+//   PJ_X: v = x64 + d (FP64), NEW / CHECK slots         -> c_x
+//   PJ_IN: v = x_in (apply entry point)                 -> c_out
 // ---------------------------------------------------------------------------
 enum { PJ_R = 0, PJ_X = 1, PJ_IN = 2 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict__ jt, const BatchDev b,
-                                                      const void* __restrict__ x_in,
-                                                      void* __restrict__ c_out) {
+__global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp,
+                                                      const void* __restrict__ x_in, void* __restrict__ c_out) {
   using CT = typename std::conditional<MODE == PJ_X, double, T>::type;
   using C = typename cx<CT>::t;
   using CO = typename cx<T>::t;
+  const BatchDev& b = *bp;
   const int g = blockIdx.x, s = blockIdx.y;
-  if (MODE == PJ_R && b.done[s]) return;
-  if (MODE == PJ_X && b.outer_done[s]) return;
+  if constexpr (MODE == PJ_R) {
+    if (b.state[s] != SL_ACTIVE) return;
+  } else if constexpr (MODE == PJ_X) {
+    const int st = b.state[s];
+    if (st != SL_NEW && st != SL_CHECK) return;
+  }
   const JuncDev& J = jt[b.junc[s]];
   if (g >= J.n_groups) return;
   __shared__ double red[32 * 2];
@@ -98,27 +145,29 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
   const int k0 = J.grp_ptr[g], k1 = J.grp_ptr[g + 1], len = k1 - k0;
   const long long vb = J.grp_voff[g];
   const long long vo = b.voff[s];
+  const long long xo = (MODE == PJ_X) ? b.xo[s] : 0;
   C acc[kMaxGroupNp];
 #pragma unroll
   for (int p = 0; p < kMaxGroupNp; ++p) acc[p] = czero<C>();
   for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
-    const long long gi = vo + J.grp_idx[kk];
+    const int gi = J.grp_idx[kk];
     C v;
     if constexpr (MODE == PJ_R) {
-      v = reinterpret_cast<const CO*>(b.r)[gi];
+      v = reinterpret_cast<const CO*>(b.r)[vo + gi];
     } else if constexpr (MODE == PJ_X) {
-      const double2 xx = b.x64[gi];
-      const double2 dd = to64(reinterpret_cast<const CO*>(b.d)[gi]);
+      const double2 xx = b.x64[xo + gi];
+      const double2 dd = to64(reinterpret_cast<const CO*>(b.d)[vo + gi]);
       v = mk2(xx.x + dd.x, xx.y + dd.y);
     } else {
-      v = reinterpret_cast<const CO*>(x_in)[gi];
+      v = reinterpret_cast<const CO*>(x_in)[vo + gi];
     }
     const long long vk = vb + (kk - k0);
 #pragma unroll
     for (int p = 0; p < kMaxGroupNp; ++p) {
       if (p < np) {
-        const CT a = (sizeof(CT) == 8) ? (CT)J.grp_val64[vk + (long long)p * len]
-                                       : (CT)J.grp_val32[vk + (long long)p * len];
+        CT a;
+        if constexpr (sizeof(CT) == 8) a = (CT)J.grp_val64[vk + (long long)p * len];
+        else a = (CT)J.grp_val32[vk + (long long)p * len];
         acc[p] = rfma(a, v, acc[p]);
       }
     }
@@ -133,141 +182,234 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Bookkeeping after each COCG iteration (one CTA): iteration counts, inner
-// convergence on the recurrence residual, breakdown detection, active count.
+// Bookkeeping after each COCG iteration, one warp per slot: rho_{k+1} and
+// ||r||^2 from the update kernel's partials (fixed-order warp tree),
+// beta_{k+1} = rho_{k+1} / rho_k, iteration counts, the recurrence target of
+// the current cycle, breakdown detection (NaN partial from the update kernel).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) inner_book_kernel(const JuncDev* __restrict__ jt, const BatchDev b,
-                                                          int max_iter) {
-  __shared__ double red[32];
-  int active = 0;
-  for (int s = threadIdx.x; s < b.nslots; s += blockDim.x) {
-    if (b.done[s]) continue;
-    const JuncDev& J = jt[b.junc[s]];
-    const int k = b.iters[s] + 1;
-    b.iters[s] = k;
-    b.total_iters[s] += 1;
-    double nrm = 0.0;
-    const double* np = b.nrm_part + (size_t)s * b.PB;
-    for (int t = 0; t < J.nB; ++t) nrm += np[t];
-    double2 mu = make_double2(0.0, 0.0);
-    const double2* mp = b.mu_part + (size_t)s * b.PA;
-    for (int t = 0; t < J.nA; ++t) { mu.x += mp[t].x; mu.y += mp[t].y; }
-    const bool bad = !isfinite(nrm) || !(mu.x != 0.0 || mu.y != 0.0);
-    if (bad) {
-      b.done[s] = 1;
-      b.breakdowns[s] += 1;
-    } else if (nrm <= b.tol2[s] || k >= max_iter) {
-      b.done[s] = 1;
-    }
-    active += b.done[s] ? 0 : 1;
+__global__ void __launch_bounds__(32 * kBookWarps) book_kernel(const JuncDev* __restrict__ jt,
+                                                              const BatchDev* __restrict__ bp, int slot_it) {
+  const BatchDev& b = *bp;
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kBookWarps + (threadIdx.x >> 5);
+  if (s >= b.nslots || b.state[s] != SL_ACTIVE) return;
+  const JuncDev& J = jt[b.junc[s]];
+  double nrm = 0.0, rx = 0.0, ry = 0.0;
+  for (int t = lane; t < J.nB; t += 32) {
+    nrm += b.nrm_part[(size_t)s * b.PB + t];
+    const double2 v = b.rho_part[(size_t)s * b.PB + t];
+    rx += v.x;
+    ry += v.y;
   }
-  double v[1] = {(double)active};
-  double out[1];
-  block_sum<1>(v, red, out);
-  if (threadIdx.x == 0) b.n_active[0] = (int)out[0];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    rx += __shfl_down_sync(0xffffffffu, rx, o);
+    ry += __shfl_down_sync(0xffffffffu, ry, o);
+  }
+  if (lane != 0) return;
+  const int k = b.iters[s] + 1;
+  b.iters[s] = k;
+  const int tot = b.total_iters[s] + 1;
+  b.total_iters[s] = tot;
+  const int cyc = b.cyc_iters[s] + 1;
+  b.cyc_iters[s] = cyc;
+  atomicAdd(b.counters, 1ull);
+  atomicAdd(b.sched + 3 + kMaxGraphIters + slot_it, 1);
+  const double2 rho = make_double2(rx, ry);
+  b.beta_cur[s] = cdiv(rho, b.rho_cur[s]);
+  b.rho_cur[s] = rho;
+  if (!isfinite(nrm)) {
+    b.restart[s] = 1;
+    b.state[s] = SL_CHECK;
+  } else if (nrm <= b.tol2[s] || tot >= b.max_iter || cyc >= b.cycle_cap) {
+    b.state[s] = SL_CHECK;
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Refinement bookkeeping after the FP64 true residual (one CTA).
+// Scheduler (one CTA, after the true-residual kernel): finishes converged
+// systems, performs reliable updates (the true FP64 residual replaces the
+// recurrence residual, the search direction is kept), frees drained slots and
+// assigns queued systems to free slots in slot order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) outer_book_kernel(const JuncDev* __restrict__ jt, const BatchDev b,
-                                                          double tol, double tol_inner, int max_outer) {
-  __shared__ double red[32];
-  int active = 0;
-  for (int s = threadIdx.x; s < b.nslots; s += blockDim.x) {
-    if (b.outer_done[s]) continue;
-    const JuncDev& J = jt[b.junc[s]];
-    double nrm = 0.0;
-    const double* np = b.nrm0_part + (size_t)s * b.PA;
-    for (int t = 0; t < J.nR; ++t) nrm += np[t];
-    const double rel = sqrt(nrm / b.bnorm2[s]);
-    b.relres[s] = rel;
-    if (rel <= tol) {
-      b.outer_done[s] = 1;
-      b.done[s] = 1;
-    } else if (!isfinite(rel) || b.n_outer[s] >= max_outer || b.breakdowns[s] > max_outer) {
-      b.outer_done[s] = 1;
-      b.done[s] = 1;
-      b.status[s] = (b.breakdowns[s] > 0 && b.n_outer[s] < max_outer) ? 2 : 1;
-    } else {
-      b.n_outer[s] += 1;
-      b.iters[s] = 0;
-      b.done[s] = 0;
-      const double t_in = tol_inner * tol_inner * nrm;
-      const double t_out = 0.25 * tol * tol * b.bnorm2[s];
-      b.tol2[s] = t_in > t_out ? t_in : t_out;
+__global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __restrict__ jt,
+                                                             const BatchDev* __restrict__ bp, int slot_it) {
+  const BatchDev& b = *bp;
+  const int S = b.nslots;
+  __shared__ int warp_cnt[32];
+  __shared__ int s_next;
+  __shared__ double red[32 * 2];
+  int upd = 0, busy = 0;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    int st = b.state[s];
+    if (st == SL_DRAIN) {
+      st = SL_FREE;
+    } else if (st == SL_NEW || st == SL_CHECK) {
+      const JuncDev& J = jt[b.junc[s]];
+      double nrm = 0.0;
+      double2 rho = make_double2(0.0, 0.0);
+      const double* np = b.nrm0_part + (size_t)s * b.PA;
+      const double2* rp = b.rho0_part + (size_t)s * b.PA;
+      for (int t = 0; t < J.nR; ++t) {
+        nrm += np[t];
+        rho.x += rp[t].x;
+        rho.y += rp[t].y;
+      }
+      if (st == SL_NEW) {
+        b.bnorm2[s] = nrm > 0.0 ? nrm : 1.0;
+        b.rlast2[s] = 4.0 * nrm;
+        b.iters[s] = 0;
+        b.total_iters[s] = 0;
+        b.n_upd[s] = 0;
+        b.restart[s] = 0;
+      }
+      const double bn2 = b.bnorm2[s];
+      const double rel = sqrt(nrm / bn2);
+      const int sy = b.sys[s];
+      const bool conv = (st == SL_CHECK && rel <= b.tol) || nrm == 0.0;
+      const bool fail = !isfinite(rel) || b.total_iters[s] >= b.max_iter || b.n_upd[s] >= b.max_upd;
+      if (conv || fail) {
+        b.out_iters[sy] = b.total_iters[s];
+        b.out_relres[sy] = rel;
+        b.out_status[sy] = conv ? 0 : (b.restart[s] ? 2 : 1);
+        st = SL_DRAIN;
+      } else {
+        // A replacement that did not cut the true residual by 4x means the
+        // inner-precision recurrence has lost its way (rounding in the Krylov
+        // basis): restart it from the true residual instead of continuing.
+        if (st == SL_CHECK && nrm > 0.0625 * b.rlast2[s]) b.restart[s] = 1;
+        b.rlast2[s] = nrm;
+        if (st == SL_NEW || b.restart[s]) {
+          // fresh start: p = r at the next iteration
+          b.iters[s] = 0;
+          b.restart[s] = 0;
+        } else {
+          // reliable update: the true residual replaces the recurrence residual
+          // and the direction update continues with beta_k = rho_new / rho_{k-1}
+          // (beta_cur holds rho_k / rho_{k-1}, rho_cur holds rho_k)
+          b.beta_cur[s] = cmul(b.beta_cur[s], cdiv(rho, b.rho_cur[s]));
+        }
+        b.rho_cur[s] = rho;
+        const double t_in = b.delta * b.delta * nrm, t_out = 0.25 * b.tol * b.tol * bn2;
+        b.tol2[s] = t_in > t_out ? t_in : t_out;
+        if (st == SL_CHECK) {
+          b.n_upd[s] += 1;
+          ++upd;
+        }
+        b.cyc_iters[s] = 0;
+        st = SL_ACTIVE;
+      }
     }
-    active += b.outer_done[s] ? 0 : 1;
+    b.state[s] = st;
   }
-  double v[1] = {(double)active};
-  double out[1];
-  block_sum<1>(v, red, out);
-  if (threadIdx.x == 0) b.n_active[1] = (int)out[0];
+  __syncthreads();
+  // assign queued systems to FREE slots, in slot order and queue (FIFO) order;
+  // a system whose dependency has not finished blocks the queue.
+  __shared__ int first_bad, stop;
+  if (threadIdx.x == 0) {
+    s_next = b.sched[0];
+    stop = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < S; base += blockDim.x) {
+    if (stop) break;  // uniform: read after a barrier
+    const int s = base + threadIdx.x;
+    const bool fr = s < S && b.state[s] == SL_FREE;
+    const unsigned m = __ballot_sync(0xffffffffu, fr);
+    if (lane == 0) warp_cnt[warp] = __popc(m);
+    if (threadIdx.x == 0) first_bad = 0x7fffffff;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) before += warp_cnt[w];
+      total += warp_cnt[w];
+    }
+    const int rank = before + __popc(m & ((1u << lane) - 1u));
+    const int next = s_next;
+    const int n = next + rank;
+    bool ready = false;
+    if (fr && n < b.nsys) {
+      const int dep = b.sys_dep ? b.sys_dep[n] : -1;
+      ready = dep < 0 || b.out_status[dep] >= 0;
+    }
+    if (fr && !ready) atomicMin(&first_bad, rank);
+    __syncthreads();
+    if (fr && rank < first_bad) {
+      b.sys[s] = n;
+      b.junc[s] = b.sys_junc[n];
+      b.E[s] = b.sys_E[n];
+      b.col[s] = b.sys_col[n];
+      const long long xo = b.sys_xo[n];
+      b.xo[s] = xo >= 0 ? xo : b.voff[s];
+      b.xfo[s] = b.sys_xfo[n];
+      b.state[s] = SL_NEW;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int assigned = total < first_bad ? total : first_bad;
+      s_next = next + assigned;
+      if (first_bad != 0x7fffffff) stop = 1;
+    }
+    __syncthreads();
+  }
+  for (int s = threadIdx.x; s < S; s += blockDim.x) busy += (b.state[s] != SL_FREE) ? 1 : 0;
+  double v[2] = {(double)busy, (double)upd};
+  double out[2];
+  block_sum<2>(v, red, out);
+  if (threadIdx.x == 0) {
+    b.sched[0] = s_next;
+    b.sched[1] = (int)out[0];
+    b.sched[3 + slot_it] = (int)out[0];
+    b.sched[3 + kMaxGraphIters + slot_it] = 0;  // counted by the bookkeeping kernel of this iteration
+    b.counters[1] += (unsigned long long)out[1];
+  }
 }
 
-// x64 += d, d = 0 for systems still being refined (runs between the true
-// residual and the refinement bookkeeping, so it sees the previous outer_done
-// flags; each thread touches only its own points).
+// x64 += d, d = 0 for slots whose true residual was just computed (each thread
+// touches only its own points).
 template <typename T>
-__global__ void __launch_bounds__(kVecThreads) x_update_kernel(const JuncDev* __restrict__ jt, const BatchDev b) {
+__global__ void __launch_bounds__(kVecThreads) x_update_kernel(const JuncDev* __restrict__ jt,
+                                                               const BatchDev* __restrict__ bp) {
   using C = typename cx<T>::t;
+  const BatchDev& b = *bp;
   const int s = blockIdx.y;
-  if (b.outer_done[s]) return;
+  const int st = b.state[s];
+  if (st != SL_NEW && st != SL_CHECK) return;
   const JuncDev& J = jt[b.junc[s]];
   if ((int)blockIdx.x >= J.nB) return;
-  const long long vo = b.voff[s];
+  const long long vo = b.voff[s], xo = b.xo[s];
   const long long i0 = (long long)blockIdx.x * kVecPts;
   const long long i1 = min(i0 + (long long)kVecPts, J.N);
   C* dv = reinterpret_cast<C*>(b.d);
   for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
     const double2 d = to64(dv[vo + i]);
-    double2 x = b.x64[vo + i];
+    double2 x = b.x64[xo + i];
     x.x += d.x;
     x.y += d.y;
-    b.x64[vo + i] = x;
+    b.x64[xo + i] = x;
     dv[vo + i] = czero<C>();
   }
 }
 
-// ||b||^2 of adjoint right-hand sides b = Gamma_L o conj(xf) (one CTA per slot).
-__global__ void __launch_bounds__(256) bnorm_adjoint_kernel(const JuncDev* __restrict__ jt, const BatchDev b) {
+// T partial of finished forward systems: out_t[sys] = sum_{i in L} Gamma_L,i |x(i)|^2.
+__global__ void __launch_bounds__(256) emit_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
   const int s = blockIdx.x;
-  if (b.outer_done[s] || b.col[s] >= 0) return;
+  if (b.state[s] != SL_DRAIN || b.out_t == nullptr || b.col[s] < 0) return;
   const JuncDev& J = jt[b.junc[s]];
   __shared__ double red[32];
-  const long long vo = b.voff[s];
+  const long long xo = b.xo[s];
   double acc = 0.0;
   for (int l = threadIdx.x; l < J.nL; l += blockDim.x) {
-    const double g = J.L_gam[l];
-    const double2 x = b.xf[vo + J.L_idx[l]];
-    acc += g * g * (x.x * x.x + x.y * x.y);
-  }
-  double v[1] = {acc};
-  double out[1];
-  block_sum<1>(v, red, out);
-  if (threadIdx.x == 0) b.bnorm2[s] = out[0] > 0.0 ? out[0] : 1.0;
-}
-
-// t_s = sum_{i in L} Gamma_L,i |x_s(i)|^2 (FP64, fixed order), written to
-// t_out[out_index[s]] (slots with out_index < 0 are idle).
-__global__ void __launch_bounds__(256) t_partial_kernel(const JuncDev* __restrict__ jt, const BatchDev b,
-                                                        const int* __restrict__ out_index,
-                                                        double* __restrict__ t_out) {
-  const int s = blockIdx.x;
-  const int o = out_index[s];
-  if (o < 0) return;
-  const JuncDev& J = jt[b.junc[s]];
-  __shared__ double red[32];
-  const long long vo = b.voff[s];
-  double acc = 0.0;
-  for (int l = threadIdx.x; l < J.nL; l += blockDim.x) {
-    const double2 x = b.x64[vo + J.L_idx[l]];
+    const double2 x = b.x64[xo + J.L_idx[l]];
     acc += J.L_gam[l] * (x.x * x.x + x.y * x.y);
   }
   double v[1] = {acc};
   double out[1];
   block_sum<1>(v, red, out);
-  if (threadIdx.x == 0) t_out[o] = out[0];
+  if (threadIdx.x == 0) b.out_t[b.sys[s]] = out[0];
 }
 
 // T[e] = 4 sum_c Gamma_R[cols[c]] t[e][c]   (one warp per energy, fixed order).
@@ -283,19 +425,20 @@ __global__ void t_final_kernel(int n_e, int n_cols, const double* __restrict__ t
   if (lane == 0) T[e] = 4.0 * acc;
 }
 
-// g[i] += sum_s wt[s] Re(lambda_s(i) x_s(i)), lambda in x64 (adjoint), x in xf.
-__global__ void __launch_bounds__(256) grad_accum_kernel(const BatchDev b, long long N, const double* __restrict__ wt,
-                                                         double* __restrict__ g) {
+// g[i] += sum_k wt[k] Re(lambda_k(i) x_k(i)) over systems k in index order
+// (lambda_k = lam + k N, x_k = x + k N).
+__global__ void __launch_bounds__(256) grad_sys_kernel(int nsys, long long N, const double2* __restrict__ lam,
+                                                       const double2* __restrict__ x, const double* __restrict__ wt,
+                                                       double* __restrict__ g) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double acc = 0.0;
-  for (int s = 0; s < b.nslots; ++s) {
-    const double w = wt[s];
+  for (int k = 0; k < nsys; ++k) {
+    const double w = wt[k];
     if (w == 0.0) continue;
-    const long long gi = b.voff[s] + i;
-    const double2 l = b.x64[gi];
-    const double2 x = b.xf[gi];
-    acc += w * (l.x * x.x - l.y * x.y);
+    const double2 l = lam[(long long)k * N + i];
+    const double2 v = x[(long long)k * N + i];
+    acc += w * (l.x * v.x - l.y * v.y);
   }
   g[i] += acc;
 }
@@ -303,21 +446,21 @@ __global__ void __launch_bounds__(256) grad_accum_kernel(const BatchDev b, long 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_op_R1(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev&,
-                         const void*, void*, const void*);
-cudaError_t launch_op_R2(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev&,
-                         const void*, void*, const void*);
-cudaError_t launch_op_R3(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev&,
-                         const void*, void*, const void*);
-cudaError_t launch_op_R4(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev&,
-                         const void*, void*, const void*);
-cudaError_t launch_op_R5(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev&,
-                         const void*, void*, const void*);
-cudaError_t launch_op_R6(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev&,
-                         const void*, void*, const void*);
+#define RSN_DECL_OP(R)                                                                                        \
+  cudaError_t launch_op_R##R(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev*, \
+                             const void*, void*, const void*);                                                 \
+  cudaError_t launch_op_tma_R##R(int, bool, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev*,  \
+                                 const void*, void*, const void*);
+RSN_DECL_OP(1)
+RSN_DECL_OP(2)
+RSN_DECL_OP(3)
+RSN_DECL_OP(4)
+RSN_DECL_OP(5)
+RSN_DECL_OP(6)
+#undef RSN_DECL_OP
 
 cudaError_t launch_op(int mode, bool fp32, int R, int ppt, dim3 grid, int threads, size_t smem, cudaStream_t st,
-                      const JuncDev* jt, const BatchDev& b, const void* x_in, void* y_out, const void* c_in) {
+                      const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out, const void* c_in) {
   switch (R) {
     case 1: return launch_op_R1(mode, fp32, ppt, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
     case 2: return launch_op_R2(mode, fp32, ppt, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
@@ -329,13 +472,40 @@ cudaError_t launch_op(int mode, bool fp32, int R, int ppt, dim3 grid, int thread
   }
 }
 
+cudaError_t launch_op_tma(int mode, bool fp32, int R, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                          const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out, const void* c_in) {
+  switch (R) {
+    case 1: return launch_op_tma_R1(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 2: return launch_op_tma_R2(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 3: return launch_op_tma_R3(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 4: return launch_op_tma_R4(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 5: return launch_op_tma_R5(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 6: return launch_op_tma_R6(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t op_tma_smem_bytes(bool fp32, int mode, int R, int nx, int ny, int n_proj) {
+  const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
+  const size_t nin = mode == OP_COCG ? 2 : 1;
+  return el * (kStages * nin * (size_t)nx * ny + 2 * (size_t)(nx + 2 * R) * (ny + 2 * R) + (size_t)n_proj) +
+         16 + 8 * kStages;
+}
+
 size_t op_smem_bytes(bool fp32, int mode, int R, int TY, int nx, int n_proj) {
   const size_t el = (mode == OP_RESID || !fp32) ? sizeof(double2) : sizeof(float2);
   return el * (2 * (size_t)(TY + 2 * R) * (nx + 2 * R) + (size_t)n_proj);
 }
 
+cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
+  dim3 grid(nB, nslots);
+  if (fp32) zero_kernel<float><<<grid, kVecThreads, 0, st>>>(jt, b);
+  else zero_kernel<double><<<grid, kVecThreads, 0, st>>>(jt, b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
-                               const BatchDev& b) {
+                               const BatchDev* b) {
   dim3 grid(nB, nslots);
   if (fp32) cocg_update_kernel<float><<<grid, kVecThreads, 0, st>>>(jt, b);
   else cocg_update_kernel<double><<<grid, kVecThreads, 0, st>>>(jt, b);
@@ -343,7 +513,7 @@ cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, c
 }
 
 cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, cudaStream_t st, const JuncDev* jt,
-                           const BatchDev& b, const void* x_in, void* c_out) {
+                           const BatchDev* b, const void* x_in, void* c_out) {
   dim3 grid(n_groups, nslots);
   if (mode == PJ_R) {
     if (fp32) project_kernel<float, PJ_R><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
@@ -358,34 +528,26 @@ cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_inner_book(int nslots, int max_iter, cudaStream_t st, const JuncDev* jt, const BatchDev& b) {
-  (void)nslots;
-  inner_book_kernel<<<1, 1024, 0, st>>>(jt, b, max_iter);
+cudaError_t launch_book(int nslots, int slot_it, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
+  book_kernel<<<(nslots + kBookWarps - 1) / kBookWarps, 32 * kBookWarps, 0, st>>>(jt, b, slot_it);
   return cudaGetLastError();
 }
 
-cudaError_t launch_outer_book(int nslots, double tol, double tol_inner, int max_outer, cudaStream_t st,
-                              const JuncDev* jt, const BatchDev& b) {
+cudaError_t launch_sched(int nslots, int slot_it, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
   (void)nslots;
-  outer_book_kernel<<<1, 1024, 0, st>>>(jt, b, tol, tol_inner, max_outer);
+  sched_kernel<<<1, kSchedThreads, 0, st>>>(jt, b, slot_it);
   return cudaGetLastError();
 }
 
-cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev& b) {
+cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
   dim3 grid(nB, nslots);
   if (fp32) x_update_kernel<float><<<grid, kVecThreads, 0, st>>>(jt, b);
   else x_update_kernel<double><<<grid, kVecThreads, 0, st>>>(jt, b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bnorm_adjoint(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev& b) {
-  bnorm_adjoint_kernel<<<nslots, 256, 0, st>>>(jt, b);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_t_partial(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev& b,
-                             const int* out_index, double* t_out) {
-  t_partial_kernel<<<nslots, 256, 0, st>>>(jt, b, out_index, t_out);
+cudaError_t launch_emit(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
+  emit_kernel<<<nslots, 256, 0, st>>>(jt, b);
   return cudaGetLastError();
 }
 
@@ -396,10 +558,9 @@ cudaError_t launch_t_final(int n_e, int n_cols, cudaStream_t st, const double* t
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_accum(int nslots, long long N, cudaStream_t st, const BatchDev& b, const double* wt,
-                              double* g) {
-  (void)nslots;
-  grad_accum_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(b, N, wt, g);
+cudaError_t launch_grad_sys(int nsys, long long N, cudaStream_t st, const double2* lam, const double2* x,
+                            const double* wt, double* g) {
+  grad_sys_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(nsys, N, lam, x, wt, g);
   return cudaGetLastError();
 }
 
