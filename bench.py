@@ -5,7 +5,7 @@ Workload (one "step"): the 24x24x120 synthetic molecular junction (69,120
 points, h = 0.35 bohr, 8th-order FD, soft-square leads, 20 Gaussian wells, 20
 atoms x 4 s/p KB projectors, 8-plane quadratic CAP, seed 1) at one energy from
 128 in [0.16, 0.24] Ha: the partial T(E) and dT(E)/dV_loc over a batch of
-1,152 right-CAP columns (every 4th of the 4,608) = 1,152 forward + 1,152
+576 right-CAP columns (every 8th of the 4,608) = 576 forward + 576
 adjoint COCG solves, FP32 Krylov recurrence with FP64 reliable updates to a
 true relative residual of 1e-10, FP64 T and gradient sums.  Every solve
 counts as one unit of the metric.
@@ -148,11 +148,17 @@ def sum_over_ranks(dist, x: float) -> float:
     return float(t.item())
 
 
+def energy_index(rank: int, world: int, k: int) -> int:
+    """Grid index of the energy of step k on `rank`: ranks take disjoint
+    energies, and consecutive steps stride across the whole window (37 is
+    coprime to 128, so the first 128 steps of all ranks never repeat one)."""
+    return ((rank + k * world) * 37) % N_ENERGIES
+
+
 def energy_for(rank: int, world: int, k: int) -> float:
-    """Energy of step k on `rank`: ranks take disjoint, interleaved energies."""
     import numpy as np
     E = np.linspace(E_LO, E_HI, N_ENERGIES)
-    return float(E[(rank + k * world) % N_ENERGIES])
+    return float(E[energy_index(rank, world, k)])
 
 
 # ---------------------------------------------------------------------------
@@ -214,7 +220,10 @@ def run_ours(args):
     n_cols = int(cols.size)
     solves_per_step = 2 * n_cols
     ctx = B.Context(local).set_junction(j)
-    opts = B.default_opts(B.RSN_MIXED, timing=1)
+    opts = B.default_opts(B.RSN_MIXED, timing=1, deadline_ms=args.deadline * 1e3)
+    # operator-kernel tile for this grid and slot count (untimed set-up)
+    tuned = ctx.autotune(B.RSN_MIXED, min(2048, max(256, solves_per_step // 4)))
+    print(f"[bench] autotuned tile {tuned}", file=sys.stderr, flush=True)
     dV = torch.empty(j.N, dtype=torch.float64, device=f"cuda:{local}")
 
     def step(k):
@@ -222,8 +231,11 @@ def run_ours(args):
         T, _ = ctx.transmission_vjp([E], [1.0], cols, opts, dV_out=dV)
         return T
 
+    t_w = time.perf_counter()
     for k in range(args.warmup):
         step(k)
+        print(f"[bench] warm-up step {k}: {time.perf_counter() - t_w:.1f} s {ctx.last_stats()}", file=sys.stderr,
+              flush=True)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -239,6 +251,7 @@ def run_ours(args):
     ub = ums = 0.0
     launches = 0
     iters = 0
+    fallbacks = 0
     for k in range(args.warmup, args.warmup + args.steps):
         step(k)
         s0, s1, st = ctx.kernel_stats(0), ctx.kernel_stats(1), ctx.last_stats()
@@ -248,7 +261,9 @@ def run_ours(args):
         ub += s1["bytes"]
         ums += s1["ms"]
         launches += st["launches"]
+        print(f"[bench] step {k}: {st} op {s0['ms']:.0f} ms / {s0['launches']}", file=sys.stderr, flush=True)
         iters += st["krylov_iters"]
+        fallbacks += st["fp64_fallbacks"]
     ev1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -290,13 +305,14 @@ def run_ours(args):
             "config": {
                 "workload": WORKLOAD, "grid": [j.nx, j.ny, j.nz], "N": j.N, "fd_order": 2 * j.fd_half_order,
                 "n_proj": j.n_proj, "columns_per_step": n_cols, "solves_per_step": solves_per_step,
-                "step": "partial T(E) + dT/dV_loc at one energy over every 4th right-CAP column: "
+                "step": "partial T(E) + dT/dV_loc at one energy over every 8th right-CAP column: "
                         "forward + adjoint COCG solve per column",
-                "energies": f"step k on rank r: E[(r + k*world) mod {N_ENERGIES}] of linspace({E_LO},{E_HI},{N_ENERGIES})",
+                "energies": f"step k on rank r: E[37 (r + k*world) mod {N_ENERGIES}] of linspace({E_LO},{E_HI},{N_ENERGIES})",
                 "tol": opts.tol, "tol_inner": opts.tol_inner,
                 "l2": "inputs larger than L2: per-step working set "
                       f"{(j.N * n_cols * (16 + 16 + 5 * 8)) / 1e9:.1f} GB",
                 "parallelism": f"replicas x{world}: energies sharded over ranks, no collective in the data path",
+                "tile": tuned,
             },
             "roofline": {
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -312,6 +328,7 @@ def run_ours(args):
                     "steps": e2e_steps},
             "gpu_launches": int(launches),
             "krylov_iters_per_solve": iters / float(args.steps * solves_per_step),
+            "fp64_fallback_solves": int(fallbacks),
             "clocks": clocks.summary(),
             "wall_s": wall,
         }
@@ -389,10 +406,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cols-per-step", type=int, default=1152,
+    ap.add_argument("--cols-per-step", type=int, default=576,
                     help="columns per step: every k-th of the 4,608 right-CAP columns (0 = all)")
-    ap.add_argument("--fp64-cols", type=int, default=288, help="columns in the FP64 comparison sample")
+    ap.add_argument("--fp64-cols", type=int, default=144, help="columns in the FP64 comparison sample")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--deadline", type=float, default=240.0, help="seconds allowed per library call")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -84,9 +84,10 @@ typedef struct {
                            (read back with rsn_kernel_stats) */
 } rsn_solver_opts;
 
-/* Defaults for a precision: FP64 -> tol 1e-13, tol_inner 1e-6;
-   MIXED -> tol 1e-10, tol_inner 1e-1; max_iter 20000, max_outer 64,
-   graphs on (16 iterations per replay), timing off. */
+/* Defaults for a precision: FP64 -> tol 1e-13, tol_inner 1e-6, max_iter 20000;
+   MIXED -> tol 1e-10, tol_inner 1e-1, max_iter 3000 (a system that needs more,
+   or whose FP32 recurrence stalls, is finished in FP64 from its iterate);
+   max_outer 64, graphs on (16 iterations per replay), timing off. */
 void rsn_default_opts(int precision, rsn_solver_opts* opts);
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`
@@ -161,10 +162,14 @@ rsn_status rsn_transmission_vjp(rsn_ctx* ctx, int n_e, const double* E, int n_co
                                 double* T);
 
 /* Counters of the last solve on this context: total Krylov iterations over all
-   columns, refinement sweeps, device kernel launches queued, and elapsed GPU
-   milliseconds of the solve phase.  Any pointer may be NULL. */
+   systems, true-residual replacements (reliable updates), device kernel
+   launches queued, elapsed GPU milliseconds of the solve phase, and the number
+   of systems that RSN_MIXED handed to FP64 because the FP32 recurrence stalled
+   (a near-singular A(E): the FP32 operator error times the condition number
+   approaches 1; such systems continue in FP64 from their iterate where it is
+   kept).  Any pointer may be NULL. */
 rsn_status rsn_last_stats(const rsn_ctx* ctx, int64_t* krylov_iters, int64_t* sweeps,
-                          int64_t* launches, double* gpu_ms);
+                          int64_t* launches, double* gpu_ms, int64_t* fp64_fallbacks);
 
 /* Live per-kernel timing of the last solve call made with opts.timing = 1.
    kind 0: the fused COCG operator kernel (p = r + beta p, q = A p, p^T q);
@@ -199,8 +204,11 @@ rsn_status rsn_autotune(rsn_ctx* ctx, int precision, int nslots, int* TY, int* L
 
 /* Override the operator kernel's tile (0 = automatic): TY rows of the x-y
    plane per CTA, Lz planes per CTA along z, ppt owned points per thread
-   (1..4).  Used by the autotuner and by tests that force ragged tiles; it does
-   not change results beyond rounding order.  Errors: RSN_EINVAL. */
+   (1..4), or ppt = -1 for the plane-streaming (bulk-copy) kernel on whole
+   planes (FP32 operator, planes of at most 1024 points with 16-byte aligned
+   sizes; other cases keep the register kernel).  Used by the autotuner and by
+   tests that force ragged tiles; it does not change results beyond rounding
+   order.  Errors: RSN_EINVAL. */
 rsn_status rsn_set_tiling(rsn_ctx* ctx, int TY, int Lz, int ppt);
 
 /* Human-readable description of the context's last error ("" if none).

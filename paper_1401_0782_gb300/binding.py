@@ -38,7 +38,7 @@ _SIGS = {
                                     ct.c_void_p]),
     "rsn_transmission_vjp": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
                                         ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
-    "rsn_last_stats": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "rsn_last_stats": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_last_error": (ct.c_char_p, [ct.c_void_p]),
     "rsn_kernel_stats": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_set_tiling": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int]),
@@ -262,7 +262,8 @@ class Context:
         return {"TY": ty.value, "Lz": lz.value, "ppt": ppt.value, "tma": tma.value, "gbs": gbs.value}
 
     def last_stats(self):
-        it, sw, la, ms = ct.c_int64(), ct.c_int64(), ct.c_int64(), ct.c_double()
+        it, sw, la, ms, fb = ct.c_int64(), ct.c_int64(), ct.c_int64(), ct.c_double(), ct.c_int64()
         self._check("rsn_last_stats", self.lib.rsn_last_stats(self.h, ct.byref(it), ct.byref(sw), ct.byref(la),
-                                                              ct.byref(ms)))
-        return {"krylov_iters": it.value, "sweeps": sw.value, "launches": la.value, "gpu_ms": ms.value}
+                                                              ct.byref(ms), ct.byref(fb)))
+        return {"krylov_iters": it.value, "sweeps": sw.value, "launches": la.value, "gpu_ms": ms.value,
+                "fp64_fallbacks": fb.value}

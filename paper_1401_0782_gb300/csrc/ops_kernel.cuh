@@ -62,8 +62,11 @@ template <typename T> struct RawIn<T, OP_COCG> { typename cx<T>::t a, b; };
 template <typename T> struct RawIn<T, OP_RESID> { double2 a; typename cx<T>::t b; };
 template <typename T> struct RawIn<T, OP_APPLY> { typename cx<T>::t a; };
 
+// At most kOpThreads threads per CTA; the minimum resident CTAs per SM bound
+// the registers per thread (64 / 85 / 128 for 1 / 2 / 3+ points per thread).
+constexpr int kOpThreads = 256;
 template <typename T, int R, int PPT, int MODE>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(kOpThreads, (PPT == 1 ? 4 : (PPT == 2 ? 3 : 2)))
 op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const void* __restrict__ x_in,
           void* __restrict__ y_out, const void* __restrict__ c_in) {
   // compute type: FP64 for the true residual, else the inner precision
@@ -72,7 +75,7 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
   using CO = typename cx<T>::t;   // storage complex of the Krylov vectors
   using Raw = RawIn<T, MODE>;
   constexpr int Q = 2 * R + 1;
-  constexpr int PF = 2;  // planes loaded ahead of use
+  constexpr int PF = 3;  // planes loaded ahead of use
 
   const BatchDev& b = *bp;
   const int s = blockIdx.y;
@@ -95,6 +98,7 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
   const long long vo = b.voff[s];
   const long long xo = (MODE == OP_RESID) ? b.xo[s] : 0;
   const double E = b.E[s];
+  const double sig = (MODE == OP_RESID) ? b.sigma[s] : 1.0;  // d is stored in units of ||b||
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm0 = reinterpret_cast<C*>(smem_raw);
@@ -189,7 +193,7 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
       return v;
     } else if constexpr (MODE == OP_RESID) {
       const double2 dd = to64(w.b);
-      return mk2(w.a.x + dd.x, w.a.y + dd.y);
+      return mk2(fma(sig, dd.x, w.a.x), fma(sig, dd.y, w.a.y));
     } else {
       return (C)w.a;
     }
@@ -219,6 +223,25 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
 
   CT acc0 = 0, acc1 = 0, acc2 = 0;  // COCG: mu(re,im) ; RESID: nrm, rho(re,im)
   CT car0 = 0, car1 = 0;            // Kahan carries of the COCG sums
+  // per-point operator data of the next plane to compute, loaded one plane early
+  float2 dgf_n[PPT];
+  int e0_n[PPT], e1_n[PPT];
+  auto load_pt = [&](int z) {
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      dgf_n[u] = make_float2(0.f, 0.f);
+      e0_n[u] = e1_n[u] = 0;
+      if (own[u] && z < z1) {
+        const long long g = (long long)z * plane + po[u];
+        if constexpr (sizeof(CT) == 4) dgf_n[u] = J.dg32[g];
+        if (n_proj > 0) {
+          e0_n[u] = J.inv_ptr[g];
+          e1_n[u] = J.inv_ptr[g + 1];
+        }
+      }
+    }
+  };
+  load_pt(z0);
   __syncthreads();
 
   for (int zc = z0 - 2 * R; zc < z1; ++zc) {
@@ -246,6 +269,15 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
       smb[(yl + R) * pitch + x + R] = produce(load_raw((long long)zc * plane + (y0 + yl) * nx + x));
     }
     __syncthreads();
+    float2 dgf_c[PPT];
+    int e0_c[PPT], e1_c[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      dgf_c[u] = dgf_n[u];
+      e0_c[u] = e0_n[u];
+      e1_c[u] = e1_n[u];
+    }
+    load_pt(zc + 1);
 
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
@@ -265,10 +297,10 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
         const double2 t = J.dg64[gl];
         y = cfma(mk2((CT)(E + t.x), (CT)t.y), vc, lap);
       } else {
-        y = fd_diff_form<C, CT, R>(qv[u], smb, so[u], pitch, wst, vc, J.dg32[gl], E);
+        y = fd_diff_form<C, CT, R>(qv[u], smb, so[u], pitch, wst, vc, dgf_c[u], E);
       }
       if (n_proj > 0) {
-        const int e0 = J.inv_ptr[gl], e1 = J.inv_ptr[gl + 1];
+        const int e0 = e0_c[u], e1 = e1_c[u];
         for (int e = e0; e < e1; ++e) {
           CT a;
           if constexpr (sizeof(CT) == 8) a = (CT)J.inv_val64[e];

@@ -67,15 +67,15 @@ struct Workspace {
   long long N = 0;
   int PA = 0, PB = 0, n_proj = 0;
   DevBuf Xslot, r, p0, p1, q, d;
-  DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, rho_cur, beta_cur;
-  DevBuf bnorm2, rlast2, tol2;
+  DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, stall, warm, rho_cur, beta_cur;
+  DevBuf bnorm2, sigma, rlast2, tol2;
   DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters;
   int generation = 0;
 };
 
 // Per-call system queue and outputs.
 struct CallBufs {
-  DevBuf sys_junc, sys_E, sys_col, sys_xo, sys_xfo, sys_dep, out_iters, out_relres, out_status, out_t;
+  DevBuf sys_junc, sys_E, sys_col, sys_xo, sys_xfo, sys_dep, sys_bn2, out_iters, out_relres, out_status, out_t;
   DevBuf X0, X1, wt, g, t_all, gr_cols, Td;
 };
 
@@ -121,13 +121,13 @@ struct rsn_ctx {
   int* sched_host = nullptr;  // pinned mirror of BatchDev::sched
 
   // stats of the last solve
-  int64_t st_iters = 0, st_sweeps = 0, st_launches = 0;
+  int64_t st_iters = 0, st_sweeps = 0, st_launches = 0, st_fallback = 0;
   double st_ms = 0.0;
   // live kernel timing (opts.timing): [0] COCG operator kernel, [1] COCG update kernel
   std::vector<cudaEvent_t> tev;  // 4 per graph iteration
   int64_t ks_launches[2] = {0, 0};
   double ks_ms[2] = {0, 0}, ks_bytes[2] = {0, 0};
-  int tile_override[4] = {0, 0, 0, 0};  // TY, Lz, ppt, no-TMA (autotuner / tests)
+  int tile_override[4] = {0, 0, 0, 0};  // TY, Lz, ppt, -1 = plane-streaming (TMA) kernel
 };
 
 static std::string g_create_err;
@@ -177,21 +177,24 @@ static void clear_graphs(rsn_ctx* c) {
 static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslots) {
   Tiling t;
   const int nx = c->nx, ny = c->ny, nz = c->nz, R = c->R;
-  const int qregs = (2 * R + 1) * (compute64 ? 4 : 2);
-  int ppt_max = std::max(1, std::min(4, 64 / qregs));
-  int TY = ny;
-  if ((long long)nx * ny > 512LL * ppt_max) {
-    const int tymax = std::max(1, (512 * ppt_max) / nx);
-    const int yt = (ny + tymax - 1) / tymax;
+  // default: one point per thread (64 registers, 4 CTAs per SM), as many whole
+  // x rows per tile as fit 256 threads; the autotuner may choose otherwise
+  int TY = std::max(1, std::min(ny, 256 / std::max(1, nx)));
+  {
+    const int yt = (ny + TY - 1) / TY;
     TY = (ny + yt - 1) / yt;
   }
-  int ppt = std::min(ppt_max, std::max(1, (nx * TY + 383) / 384));
+  int ppt = 1;
   if (c->tile_override[0] > 0) TY = std::min(ny, c->tile_override[0]);
   if (c->tile_override[2] > 0) ppt = std::min(4, c->tile_override[2]);
   int threads = (nx * TY + ppt - 1) / ppt;
   threads = ((threads + 31) / 32) * 32;
-  while (threads > 512 && ppt < 4) {
+  while (threads > 256 && ppt < 4) {
     ++ppt;
+    threads = (((nx * TY + ppt - 1) / ppt) + 31) / 32 * 32;
+  }
+  while (threads > 256 && TY > 1) {  // still too many: split the plane into more y tiles
+    TY = (TY + 1) / 2;
     threads = (((nx * TY + ppt - 1) / ppt) + 31) / 32 * 32;
   }
   t.TY = TY;
@@ -210,8 +213,11 @@ static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslo
   // keep every bulk copy 16-byte aligned; an explicit TY or ppt selects the
   // register-prefetch kernel instead
   const long long pl = (long long)nx * ny;
-  if (!compute64 && mode != OP_RESID && t.ytiles == 1 && pl <= 1024 && (pl * 8) % 16 == 0 &&
-      (c->N * 8) % 16 == 0 && c->tile_override[0] == 0 && c->tile_override[2] == 0 && c->tile_override[3] == 0) {
+  if (!compute64 && mode != OP_RESID && pl <= 1024 && (pl * 8) % 16 == 0 && (c->N * 8) % 16 == 0 &&
+      c->tile_override[3] == -1) {
+    t.TY = ny;
+    t.ytiles = 1;
+    t.n = t.ztiles;
     const size_t sm = op_tma_smem_bytes(true, mode, R, nx, ny, c->n_proj);
     if (sm <= 200 * 1024) {
       t.tma = true;
@@ -397,11 +403,12 @@ void rsn_default_opts(int precision, rsn_solver_opts* o) {
   if (o->precision == RSN_MIXED) {
     o->tol = 1e-10;
     o->tol_inner = 1e-1;
+    o->max_iter = 3000;  // slower systems are handed to the FP64 fallback
   } else {
     o->tol = 1e-13;
     o->tol_inner = 1e-6;
+    o->max_iter = 20000;
   }
-  o->max_iter = 20000;
   o->max_outer = 64;
   o->deadline_ms = 0.0;
   o->rhs_block = 0;
@@ -558,8 +565,9 @@ rsn_status rsn_kernel_stats(const rsn_ctx* c, int kind, int64_t* launches, doubl
   return RSN_OK;
 }
 
-rsn_status rsn_last_stats(const rsn_ctx* c, int64_t* it, int64_t* sw, int64_t* la, double* ms) {
+rsn_status rsn_last_stats(const rsn_ctx* c, int64_t* it, int64_t* sw, int64_t* la, double* ms, int64_t* fb) {
   if (!c) return RSN_EINVAL;
+  if (fb) *fb = c->st_fallback;
   if (it) *it = c->st_iters;
   if (sw) *sw = c->st_sweeps;
   if (la) *la = c->st_launches;
@@ -635,9 +643,12 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   RSN_CUDA(c, w.cyc_iters.ensure(si));
   RSN_CUDA(c, w.n_upd.ensure(si));
   RSN_CUDA(c, w.restart.ensure(si));
+  RSN_CUDA(c, w.stall.ensure(si));
+  RSN_CUDA(c, w.warm.ensure(si));
   RSN_CUDA(c, w.rho_cur.ensure(S * sizeof(double2)));
   RSN_CUDA(c, w.beta_cur.ensure(S * sizeof(double2)));
   RSN_CUDA(c, w.bnorm2.ensure(sd));
+  RSN_CUDA(c, w.sigma.ensure(sd));
   RSN_CUDA(c, w.rlast2.ensure(sd));
   RSN_CUDA(c, w.tol2.ensure(sd));
   RSN_CUDA(c, w.rho0.ensure((size_t)S * PA * sizeof(double2)));
@@ -675,6 +686,7 @@ static rsn_status ensure_calls(rsn_ctx* c, long long nsys) {
   RSN_CUDA(c, q.sys_xo.ensure(n * sizeof(long long)));
   RSN_CUDA(c, q.sys_xfo.ensure(n * sizeof(long long)));
   RSN_CUDA(c, q.sys_dep.ensure(n * sizeof(int)));
+  RSN_CUDA(c, q.sys_bn2.ensure(n * sizeof(double)));
   RSN_CUDA(c, q.out_iters.ensure(n * sizeof(int)));
   RSN_CUDA(c, q.out_relres.ensure(n * sizeof(double)));
   RSN_CUDA(c, q.out_status.ensure(n * sizeof(int)));
@@ -687,15 +699,25 @@ static rsn_status ensure_calls(rsn_ctx* c, long long nsys) {
 // ---------------------------------------------------------------------------
 struct StreamIn {
   std::vector<int> junc, col, dep;
-  std::vector<double> E;
+  std::vector<double> E, bn2;
   std::vector<long long> xo, xfo;
   void resize(size_t n) {
     junc.assign(n, 0);
     col.assign(n, 0);
     dep.assign(n, -1);
     E.assign(n, 0.0);
+    bn2.assign(n, 0.0);
     xo.assign(n, -1);
     xfo.assign(n, 0);
+  }
+  void push(const StreamIn& o, size_t k) {
+    junc.push_back(o.junc[k]);
+    col.push_back(o.col[k]);
+    dep.push_back(o.dep[k]);
+    E.push_back(o.E[k]);
+    bn2.push_back(o.bn2[k]);
+    xo.push_back(o.xo[k]);
+    xfo.push_back(o.xfo[k]);
   }
 };
 struct StreamOut {
@@ -726,9 +748,12 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.cyc_iters = w.cyc_iters.as<int>();
   b.n_upd = w.n_upd.as<int>();
   b.restart = w.restart.as<int>();
+  b.stall = w.stall.as<int>();
+  b.warm = w.warm.as<int>();
   b.rho_cur = w.rho_cur.as<double2>();
   b.beta_cur = w.beta_cur.as<double2>();
   b.bnorm2 = w.bnorm2.as<double>();
+  b.sigma = w.sigma.as<double>();
   b.rlast2 = w.rlast2.as<double>();
   b.tol2 = w.tol2.as<double>();
   b.x64 = w.Xslot.as<double2>();
@@ -752,6 +777,7 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.max_iter = o->max_iter;
   b.max_upd = o->max_outer;
   b.cycle_cap = std::max(32, std::min(o->max_iter, 400));
+  b.stall_cap = o->precision == RSN_MIXED ? 3 : 0;
   return b;
 }
 
@@ -775,6 +801,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   RSN_CUDA(c, cudaMemcpyAsync(q.sys_xo.p, in.xo.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice, st));
   RSN_CUDA(c, cudaMemcpyAsync(q.sys_xfo.p, in.xfo.data(), nsys * sizeof(long long), cudaMemcpyHostToDevice, st));
   RSN_CUDA(c, cudaMemcpyAsync(q.sys_dep.p, in.dep.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
+  RSN_CUDA(c, cudaMemcpyAsync(q.sys_bn2.p, in.bn2.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, st));
   RSN_CUDA(c, cudaMemsetAsync(q.out_status.p, 0xff, nsys * sizeof(int), st));
   RSN_CUDA(c, cudaMemsetAsync(q.out_iters.p, 0, nsys * sizeof(int), st));
   RSN_CUDA(c, cudaMemsetAsync(q.out_relres.p, 0, nsys * sizeof(double), st));
@@ -794,6 +821,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   b.sys_xo = q.sys_xo.as<long long>();
   b.sys_xfo = q.sys_xfo.as<long long>();
   b.sys_dep = q.sys_dep.as<int>();
+  b.sys_bn2 = q.sys_bn2.as<double>();
   b.out_iters = q.out_iters.as<int>();
   b.out_relres = q.out_relres.as<double>();
   b.out_status = q.out_status.as<int>();
@@ -868,9 +896,13 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   }
 
   // every system needs at most max_iter COCG iterations plus one iteration per
-  // true residual; this bounds the replays even if the device state were wrong
+  // true residual, and a dependent system starts after its dependency; this
+  // bounds the replays even if the device state were wrong
   const long long waves = (nsys + S - 1) / S;
-  const long long max_replays = (waves * ((long long)o->max_iter + 2LL * o->max_outer + 8) + G) / G + 4;
+  bool has_dep = false;
+  for (long long k = 0; k < nsys && !has_dep; ++k) has_dep = in.dep[k] >= 0;
+  const long long per_sys = (long long)o->max_iter + 2LL * o->max_outer + 8;
+  const long long max_replays = ((waves + (has_dep ? 2 : 1)) * per_sys + G) / G + 4;
   bool timeout = false, finished = false;
   int* hs = c->sched_host;
   for (long long rep = 0; rep < max_replays; ++rep) {
@@ -929,16 +961,29 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
 }
 
 // classify finished systems into an overall status; fills iters/relres
-static rsn_status stream_status(const StreamOut& r, long long n0, long long n, int32_t* iters, double* relres) {
+static rsn_status stream_status(const StreamOut& r, long long n0, long long n, int32_t* iters, double* relres,
+                                std::string* why = nullptr) {
   rsn_status worst = RSN_OK;
+  long long nbad = 0;
   for (long long k = 0; k < n; ++k) {
     const int stt = r.status[n0 + k];
     const bool ok = stt == 0;
     if (iters) iters[k] = ok ? r.iters[n0 + k] : -std::max(1, r.iters[n0 + k]);
     if (relres) relres[k] = r.relres[n0 + k];
-    if (!ok && worst == RSN_OK)
-      worst = (stt < 0 || r.timeout) ? RSN_ETIMEOUT : (stt == 2 ? RSN_EBREAKDOWN : RSN_ENOCONV);
+    if (!ok) {
+      if (worst == RSN_OK) {
+        worst = (stt < 0 || r.timeout) ? RSN_ETIMEOUT : (stt == 2 ? RSN_EBREAKDOWN : RSN_ENOCONV);
+        if (why) {
+          char buf[256];
+          snprintf(buf, sizeof(buf), "system %lld: status %d after %d iterations, relative residual %.3e", n0 + k,
+                   stt, r.iters[n0 + k], r.relres[n0 + k]);
+          *why = buf;
+        }
+      }
+      ++nbad;
+    }
   }
+  if (why && nbad) *why += " (" + std::to_string(nbad) + " of " + std::to_string(n) + " systems failed)";
   return worst;
 }
 
@@ -959,7 +1004,7 @@ static rsn_status check_solve_args(rsn_ctx* c, int n_e, const double* E, int n_c
 }
 
 static void reset_stats(rsn_ctx* c) {
-  c->st_iters = c->st_sweeps = c->st_launches = 0;
+  c->st_iters = c->st_sweeps = c->st_launches = c->st_fallback = 0;
   for (int k = 0; k < 2; ++k) c->ks_launches[k] = 0, c->ks_ms[k] = 0, c->ks_bytes[k] = 0;
 }
 
@@ -1042,14 +1087,44 @@ rsn_status rsn_solve_columns(rsn_ctx* c, int n_e, const double* E, int n_cols, c
   StreamOut so;
   if ((rs = run_stream(c, o, in, reinterpret_cast<double2*>(x_dev), nullptr, false, 0, t_start, so)) != RSN_OK)
     return rs;
-  const rsn_status worst = stream_status(so, 0, nsys, iters, relres);
+  if (o->precision == RSN_MIXED) {
+    // systems whose FP32 recurrence stalled continue in FP64 from their iterate
+    std::vector<long long> F;
+    StreamIn sub;
+    for (long long k = 0; k < nsys; ++k)
+      if (so.status[k] != 0) {
+        F.push_back(k);
+        sub.push(in, (size_t)k);
+        sub.bn2.back() = 1.0;  // unit right-hand side, warm start
+      }
+    if (!F.empty()) {
+      rsn_solver_opts o64;
+      rsn_default_opts(RSN_FP64, &o64);
+      o64.tol = o->tol;
+      o64.deadline_ms = o->deadline_ms;
+      o64.use_graph = o->use_graph;
+      o64.graph_iters = o->graph_iters;
+      StreamOut s2;
+      if ((rs = run_stream(c, &o64, sub, reinterpret_cast<double2*>(x_dev), nullptr, false, 0, t_start, s2)) !=
+          RSN_OK)
+        return rs;
+      for (size_t f = 0; f < F.size(); ++f) {
+        so.status[F[f]] = s2.status[f];
+        so.iters[F[f]] += s2.iters[f];
+        so.relres[F[f]] = s2.relres[f];
+      }
+      c->st_fallback += (int64_t)F.size();
+    }
+  }
+  std::string why;
+  const rsn_status worst = stream_status(so, 0, nsys, iters, relres, &why);
   RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
   RSN_CUDA(c, cudaEventSynchronize(c->t1));
   float ms = 0;
   cudaEventElapsedTime(&ms, c->t0, c->t1);
   c->st_ms = ms;
   if ((rs = leave(c)) != RSN_OK) return rs;
-  if (worst != RSN_OK) RSN_FAIL(c, worst, "some columns did not reach tol (status %d)", (int)worst);
+  if (worst != RSN_OK) RSN_FAIL(c, worst, "some columns did not reach tol: %s", why.c_str());
   return RSN_OK;
 }
 
@@ -1078,6 +1153,7 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
   const auto t_start = std::chrono::steady_clock::now();
   RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
   rsn_status worst = RSN_OK;
+  std::string why;
   // energies per chunk: the adjoint keeps the forward and adjoint solutions of a
   // chunk (2 * chunk * n_cols * N complex128) resident
   int chunk = n_e;
@@ -1112,9 +1188,58 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
     }
     StreamOut so;
     if ((rs = run_stream(c, o, in, X, X, true, reserved, t_start, so)) != RSN_OK) return rs;
-    rsn_status bs = stream_status(so, 0, (long long)in.E.size(), nullptr, nullptr);
-    if (worst == RSN_OK) worst = bs;
-    RSN_CUDA(c, launch_t_final(ne, n_cols, c->st, q.out_t.as<double>(), q.gr_cols.as<double>(),
+    const long long NS = (long long)in.E.size();
+    RSN_CUDA(c, q.t_all.ensure(NS * sizeof(double)));
+    RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, q.out_t.p, NS * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    if (o->precision == RSN_MIXED) {
+      // systems whose FP32 recurrence stalled are re-solved in FP64: forward
+      // systems warm-start from their kept iterate (vjp) or restart (T only);
+      // an adjoint is redone whenever it or its forward system is
+      std::vector<long long> F;
+      StreamIn sub;
+      std::vector<int> pos(NS, -1);
+      for (long long k = 0; k < (adjoint ? M : NS); ++k)
+        if (so.status[k] != 0) {
+          pos[k] = (int)F.size();
+          F.push_back(k);
+          sub.push(in, (size_t)k);
+          sub.bn2.back() = adjoint ? 1.0 : 0.0;
+        }
+      if (adjoint)
+        for (long long k = M; k < 2 * M; ++k)
+          if (so.status[k] != 0 || pos[k - M] >= 0) {
+            F.push_back(k);
+            sub.push(in, (size_t)k);
+            sub.bn2.back() = 0.0;  // cold start (the right-hand side may have changed)
+            sub.dep.back() = pos[k - M];
+          }
+      if (!F.empty()) {
+        rsn_solver_opts o64;
+        rsn_default_opts(RSN_FP64, &o64);
+        o64.tol = o->tol;
+        o64.deadline_ms = o->deadline_ms;
+        o64.use_graph = o->use_graph;
+        o64.graph_iters = o->graph_iters;
+        StreamOut s2;
+        if ((rs = run_stream(c, &o64, sub, X, X, true, reserved, t_start, s2)) != RSN_OK) return rs;
+        for (size_t f = 0; f < F.size(); ++f) {
+          so.status[F[f]] = s2.status[f];
+          so.iters[F[f]] += s2.iters[f];
+          so.relres[F[f]] = s2.relres[f];
+          if (F[f] < M || !adjoint)
+            RSN_CUDA(c, cudaMemcpyAsync(q.t_all.as<double>() + F[f], q.out_t.as<double>() + f, sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->st));
+        }
+        c->st_fallback += (int64_t)F.size();
+      }
+    }
+    std::string w1;
+    rsn_status bs = stream_status(so, 0, (long long)in.E.size(), nullptr, nullptr, &w1);
+    if (worst == RSN_OK && bs != RSN_OK) {
+      worst = bs;
+      why = (adjoint ? "(forward systems 0.." + std::to_string(M - 1) + ", adjoint after) " : std::string()) + w1;
+    }
+    RSN_CUDA(c, launch_t_final(ne, n_cols, c->st, q.t_all.as<double>(), q.gr_cols.as<double>(),
                                q.Td.as<double>() + e0));
     c->st_launches += 1;
     if (adjoint) {
@@ -1141,7 +1266,7 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
   cudaEventElapsedTime(&ms, c->t0, c->t1);
   c->st_ms = ms;
   if ((rs = leave(c)) != RSN_OK) return rs;
-  if (worst != RSN_OK) RSN_FAIL(c, worst, "some columns did not reach tol (status %d)", (int)worst);
+  if (worst != RSN_OK) RSN_FAIL(c, worst, "some systems did not reach tol: %s", why.c_str());
   return RSN_OK;
 }
 
@@ -1176,6 +1301,7 @@ static rsn_status bench_kernel_impl(rsn_ctx* c, int precision, int kind, int S, 
   RSN_CUDA(c, cudaMemsetAsync(w.Xslot.p, 0x3c, vb * sizeof(double2), st));
   RSN_CUDA(c, cudaMemsetAsync(w.rho.p, 0x3f, (size_t)S * w.PB * sizeof(double2), st));
   RSN_CUDA(c, cudaMemsetAsync(w.rho_cur.p, 0x3f, S * sizeof(double2), st));
+  RSN_CUDA(c, cudaMemsetAsync(w.sigma.p, 0, S * sizeof(double), st));
   RSN_CUDA(c, cudaMemsetAsync(w.beta_cur.p, 0x3f, S * sizeof(double2), st));
   RSN_CUDA(c, cudaMemsetAsync(w.nrm.p, 0x3f, (size_t)S * w.PB * sizeof(double), st));
   RSN_CUDA(c, cudaMemsetAsync(w.mu.p, 0x3f, (size_t)S * w.PA * sizeof(double2), st));
@@ -1255,12 +1381,12 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
     const int lz = (c->nz + zt - 1) / zt;
     if (lz >= 2 * c->R + 2 || zt == 1) lzs.push_back(lz);
   }
-  for (int lz : lzs) cands.push_back({0, lz, 0, 0});
+  for (int lz : lzs) cands.push_back({0, lz, 0, -1});
   for (int p = 1; p <= 4; ++p)
     for (int ty : {c->ny, (c->ny + 1) / 2, (c->ny + 2) / 3})
       for (int lz : lzs) {
         const int thr = (c->nx * ty + p - 1) / p;
-        if (thr < 32 || thr > 512) continue;
+        if (thr < 32 || thr > 256) continue;
         cands.push_back({ty, lz, p, 1});
       }
   const int save[4] = {c->tile_override[0], c->tile_override[1], c->tile_override[2], c->tile_override[3]};
@@ -1296,7 +1422,7 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
   if (TY) *TY = bestc.TY;
   if (Lz) *Lz = bestc.Lz;
   if (ppt) *ppt = bestc.ppt;
-  if (tma) *tma = bestc.notma ? 0 : 1;
+  if (tma) *tma = bestc.notma == -1 ? 1 : 0;
   if (best_gbs) *best_gbs = best;
   (void)fp32;
   return leave(c);
@@ -1305,11 +1431,11 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
 // Tiling override used by the autotuner and the tests: TY, Lz, ppt (0 = auto).
 rsn_status rsn_set_tiling(rsn_ctx* c, int TY, int Lz, int ppt) {
   if (!c) return RSN_EINVAL;
-  if (TY < 0 || Lz < 0 || ppt < 0 || ppt > 4) RSN_FAIL(c, RSN_EINVAL, "bad tiling override");
+  if (TY < 0 || Lz < 0 || ppt < -1 || ppt > 4) RSN_FAIL(c, RSN_EINVAL, "bad tiling override");
   c->tile_override[0] = TY;
   c->tile_override[1] = Lz;
-  c->tile_override[2] = ppt;
-  c->tile_override[3] = 0;
+  c->tile_override[2] = ppt > 0 ? ppt : 0;
+  c->tile_override[3] = ppt == -1 ? -1 : 0;
   clear_graphs(c);
   c->ws.generation++;
   c->ws.slots = 0;  // partial strides may change

@@ -84,9 +84,12 @@ struct BatchDev {
   int* cyc_iters;       // COCG iterations since the last true residual
   int* n_upd;           // reliable updates so far
   int* restart;         // breakdown seen: restart with p = r at the next update
+  int* stall;           // consecutive true residuals that did not improve 4x
+  int* warm;            // the system starts from the iterate already in x64
   double2* rho_cur;     // rho_k = r^T r of the current iteration (set by book / sched)
   double2* beta_cur;    // beta_k = rho_k / rho_{k-1} for the direction update of iteration k
   double* bnorm2;
+  double* sigma;        // ||b||: the inner-precision vectors hold r / sigma and d / sigma
   double* rlast2;       // true ||r||^2 at the previous replacement (progress check)
   double* tol2;         // recurrence target ||r||^2 of the current cycle
   // vectors
@@ -114,9 +117,11 @@ struct BatchDev {
   const long long* sys_xo;   // x64 offset of each system (-1: slot storage)
   const long long* sys_xfo;
   const int* sys_dep;        // system that must finish first (adjoint after forward), -1 none
+  const double* sys_bn2;     // known ||b||^2 of a warm-started system (> 0: warm start), may be null
   int* out_iters;
   double* out_relres;
-  int* out_status;           // -1 pending, 0 converged, 1 not converged, 2 breakdown
+  int* out_status;           // -1 pending, 0 converged, 1 not converged, 2 breakdown,
+                             // 3 stalled (precision-limited: re-solve in FP64)
   double* out_t;             // T partial sum_{i in L} Gamma_L |x(i)|^2 per system (may be null)
   int* sched;                // [0] next system, [1] busy slots, [3 + it] busy after iteration it of a
                              // replay, [3 + kMaxGraphIters + it] systems that did a COCG iteration
@@ -125,6 +130,7 @@ struct BatchDev {
   double tol, delta;
   int max_iter, max_upd;
   int cycle_cap;  // a cycle longer than this ends with a true residual even if its target was not met
+  int stall_cap;  // stalled true residuals in a row before a system is handed back (0 = never)
 };
 
 enum OpMode { OP_COCG = 0, OP_RESID = 1, OP_APPLY = 2 };

@@ -36,8 +36,9 @@ __global__ void __launch_bounds__(kVecThreads) zero_kernel(const JuncDev* __rest
   const long long vo = b.voff[s], xo = b.xo[s];
   const long long i0 = (long long)blockIdx.x * kVecPts, i1 = min(i0 + (long long)kVecPts, J.N);
   C* dv = reinterpret_cast<C*>(b.d);
+  const bool keep_x = b.warm[s] != 0;
   for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
-    b.x64[xo + i] = make_double2(0.0, 0.0);
+    if (!keep_x) b.x64[xo + i] = make_double2(0.0, 0.0);
     dv[vo + i] = czero<C>();
   }
 }
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
   const long long vb = J.grp_voff[g];
   const long long vo = b.voff[s];
   const long long xo = (MODE == PJ_X) ? b.xo[s] : 0;
+  const double sig = (MODE == PJ_X) ? b.sigma[s] : 1.0;
   C acc[kMaxGroupNp];
 #pragma unroll
   for (int p = 0; p < kMaxGroupNp; ++p) acc[p] = czero<C>();
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
     } else if constexpr (MODE == PJ_X) {
       const double2 xx = b.x64[xo + gi];
       const double2 dd = to64(reinterpret_cast<const CO*>(b.d)[vo + gi]);
-      v = mk2(xx.x + dd.x, xx.y + dd.y);
+      v = mk2(fma(sig, dd.x, xx.x), fma(sig, dd.y, xx.y));
     } else {
       v = reinterpret_cast<const CO*>(x_in)[vo + gi];
     }
@@ -257,8 +259,12 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
         rho.y += rp[t].y;
       }
       if (st == SL_NEW) {
-        b.bnorm2[s] = nrm > 0.0 ? nrm : 1.0;
+        // cold start: r = b, so ||b||^2 = nrm; warm start: ||b||^2 is given
+        const double bn = b.warm[s] ? b.sys_bn2[b.sys[s]] : nrm;
+        b.bnorm2[s] = bn > 0.0 ? bn : 1.0;
+        b.sigma[s] = bn > 0.0 ? sqrt(bn) : 1.0;
         b.rlast2[s] = 4.0 * nrm;
+        b.stall[s] = 0;
         b.iters[s] = 0;
         b.total_iters[s] = 0;
         b.n_upd[s] = 0;
@@ -267,18 +273,24 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
       const double bn2 = b.bnorm2[s];
       const double rel = sqrt(nrm / bn2);
       const int sy = b.sys[s];
-      const bool conv = (st == SL_CHECK && rel <= b.tol) || nrm == 0.0;
-      const bool fail = !isfinite(rel) || b.total_iters[s] >= b.max_iter || b.n_upd[s] >= b.max_upd;
+      const bool conv = ((st == SL_CHECK || b.warm[s]) && rel <= b.tol) || nrm == 0.0;
+      // a true residual that did not improve 4x on the previous one
+      const bool no_gain = st == SL_CHECK && nrm > 0.0625 * b.rlast2[s];
+      const int stall = no_gain ? b.stall[s] + 1 : 0;
+      const bool stalled = b.stall_cap > 0 && stall >= b.stall_cap;
+      const bool fail = !isfinite(rel) || b.total_iters[s] >= b.max_iter || b.n_upd[s] >= b.max_upd || stalled;
       if (conv || fail) {
         b.out_iters[sy] = b.total_iters[s];
         b.out_relres[sy] = rel;
-        b.out_status[sy] = conv ? 0 : (b.restart[s] ? 2 : 1);
+        b.out_status[sy] = conv ? 0 : (stalled ? 3 : (b.restart[s] ? 2 : 1));
         st = SL_DRAIN;
       } else {
         // A replacement that did not cut the true residual by 4x means the
         // inner-precision recurrence has lost its way (rounding in the Krylov
         // basis): restart it from the true residual instead of continuing.
-        if (st == SL_CHECK && nrm > 0.0625 * b.rlast2[s]) b.restart[s] = 1;
+        b.stall[s] = stall;
+        if (no_gain) b.restart[s] = 1;
+        const double2 rho_s = make_double2(rho.x / bn2, rho.y / bn2);  // r^T r of r / sigma
         b.rlast2[s] = nrm;
         if (st == SL_NEW || b.restart[s]) {
           // fresh start: p = r at the next iteration
@@ -288,10 +300,11 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
           // reliable update: the true residual replaces the recurrence residual
           // and the direction update continues with beta_k = rho_new / rho_{k-1}
           // (beta_cur holds rho_k / rho_{k-1}, rho_cur holds rho_k)
-          b.beta_cur[s] = cmul(b.beta_cur[s], cdiv(rho, b.rho_cur[s]));
+          b.beta_cur[s] = cmul(b.beta_cur[s], cdiv(rho_s, b.rho_cur[s]));
         }
-        b.rho_cur[s] = rho;
-        const double t_in = b.delta * b.delta * nrm, t_out = 0.25 * b.tol * b.tol * bn2;
+        b.rho_cur[s] = rho_s;
+        // targets in the inner vectors' units (r / sigma, sigma^2 = ||b||^2)
+        const double t_in = b.delta * b.delta * nrm / bn2, t_out = 0.25 * b.tol * b.tol;
         b.tol2[s] = t_in > t_out ? t_in : t_out;
         if (st == SL_CHECK) {
           b.n_upd[s] += 1;
@@ -344,6 +357,7 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
       const long long xo = b.sys_xo[n];
       b.xo[s] = xo >= 0 ? xo : b.voff[s];
       b.xfo[s] = b.sys_xfo[n];
+      b.warm[s] = (b.sys_bn2 != nullptr && b.sys_bn2[n] > 0.0) ? 1 : 0;
       b.state[s] = SL_NEW;
     }
     __syncthreads();
@@ -367,8 +381,12 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
   }
 }
 
-// x64 += d, d = 0 for slots whose true residual was just computed (each thread
-// touches only its own points).
+// After a true residual (NEW or CHECK slots): x64 += sigma d, d = 0, and the
+// inner-precision residual is rescaled to r / sigma, sigma = ||b||, so the
+// inner recurrence works on O(1) numbers whatever the size of b (an adjoint
+// right-hand side Gamma_L o conj(x) can be ~1e-6 or smaller, whose squares
+// would leave the FP32 range).  For a NEW slot sigma comes from the residual
+// partials (r = b there); each thread touches only its own points.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) x_update_kernel(const JuncDev* __restrict__ jt,
                                                                const BatchDev* __restrict__ bp) {
@@ -379,17 +397,39 @@ __global__ void __launch_bounds__(kVecThreads) x_update_kernel(const JuncDev* __
   if (st != SL_NEW && st != SL_CHECK) return;
   const JuncDev& J = jt[b.junc[s]];
   if ((int)blockIdx.x >= J.nB) return;
+  __shared__ double s_part[64];
+  __shared__ double s_sig;
+  if (st == SL_NEW) {
+    for (int t = threadIdx.x; t < J.nR && t < 64; t += blockDim.x) s_part[t] = b.nrm0_part[(size_t)s * b.PA + t];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double n2 = 0.0;
+      for (int t = 0; t < J.nR && t < 64; ++t) n2 += s_part[t];
+      s_sig = n2 > 0.0 ? sqrt(n2) : 1.0;
+      if (blockIdx.x == 0) b.sigma[s] = s_sig;
+    }
+  } else if (threadIdx.x == 0) {
+    s_sig = b.sigma[s];
+  }
+  __syncthreads();
+  const double sig = s_sig;
+  const T isig = (T)(1.0 / sig);
   const long long vo = b.voff[s], xo = b.xo[s];
   const long long i0 = (long long)blockIdx.x * kVecPts;
   const long long i1 = min(i0 + (long long)kVecPts, J.N);
   C* dv = reinterpret_cast<C*>(b.d);
+  C* rv = reinterpret_cast<C*>(b.r);
   for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
     const double2 d = to64(dv[vo + i]);
     double2 x = b.x64[xo + i];
-    x.x += d.x;
-    x.y += d.y;
+    x.x = fma(sig, d.x, x.x);
+    x.y = fma(sig, d.y, x.y);
     b.x64[xo + i] = x;
     dv[vo + i] = czero<C>();
+    C r = rv[vo + i];
+    r.x *= isig;
+    r.y *= isig;
+    rv[vo + i] = r;
   }
 }
 

@@ -39,7 +39,7 @@ JUNCTIONS = {
 
 
 @pytest.mark.parametrize("name", sorted(JUNCTIONS))
-@pytest.mark.parametrize("tiling", [(0, 0, 0), (5, 7, 2), (3, 9, 1)])
+@pytest.mark.parametrize("tiling", [(0, 0, 0), (5, 7, 2), (3, 9, 1), (0, 11, -1)])
 def test_apply_matches_oracle_operator(B, name, tiling):
     j = JUNCTIONS[name]()
     ctx = B.Context(0).set_junction(j)
