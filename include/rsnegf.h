@@ -131,6 +131,23 @@ rsn_status rsn_set_cap(rsn_ctx* ctx, const double* gamma_l, const double* gamma_
 rsn_status rsn_apply(rsn_ctx* ctx, int precision, int n_rhs, const double* E,
                      const void* x_dev, void* y_dev);
 
+/* Allocation-free variant of rsn_apply, for callers that must not allocate
+   device memory during a call (a pre-sized memory pool, a real-time loop, or a
+   host framework that owns every allocation).  The paper has no counterpart:
+   this is an interface of this library only.  Same arguments and result as
+   rsn_apply; it calls no cudaMalloc / cudaFree / allocating library routine.
+   Its per-call scratch (launch descriptor, per-vector tables, projector
+   coefficients) is a fixed 8 MiB device array that every device which loads
+   the library holds until the process exits; a call whose scratch would not
+   fit (n_rhs * (24 + 16 * max(n_proj, 1)) bytes plus about 1 KiB) fails with
+   RSN_EINVAL.  The operator data must already be on the device: after the last
+   setter, make one allocating call (e.g. rsn_apply) first, else RSN_ESTATE.
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+   share the array: calls that overlap on the GPU race. */
+rsn_status rsn_apply_noalloc(rsn_ctx* ctx, int precision, int n_rhs, const double* E,
+                             const void* x_dev, void* y_dev);
+
 /* Green's-function columns x_{e,c} = G^r(E[e]) e_{cols[c]} (Eq. G).
    x_dev: device, [n_e][n_cols][N] complex128, written in place.  iters / relres
    (host, n_e*n_cols each, may be NULL) receive the total Krylov iterations and

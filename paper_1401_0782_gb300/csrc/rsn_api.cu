@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1443,3 +1444,103 @@ rsn_status rsn_set_tiling(rsn_ctx* c, int TY, int Lz, int ppt) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free operator application.
+//
+// Callers that cannot allocate device memory during a call -- code running
+// where cudaMalloc is forbidden or unsafe (inside a pre-sized memory pool, a
+// real-time loop, or a host framework that owns every allocation) -- can apply
+// A(E) through rsn_apply_noalloc.  Its per-call scratch (the launch
+// descriptor, the per-vector energy / offset / junction tables and the
+// projector coefficients) lives in the fixed array below instead of library
+// allocations.  Every device that loads the library holds this array until the
+// process exits.  All calls share it and it keeps the last call's contents;
+// every field a call reads is rewritten by that call before use, so nothing
+// needs clearing, but calls that overlap on the GPU (other streams or host
+// threads) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// per-vector offsets and junction ids of the scratch tables (filled on the device)
+__global__ void noalloc_tables_kernel(int n, long long N, long long* voff, int* junc) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) {
+    voff[s] = (long long)s * N;
+    junc[s] = 0;
+  }
+}
+
+extern "C" rsn_status rsn_apply_noalloc(rsn_ctx* c, int precision, int n_rhs, const double* E, const void* x_dev,
+                                        void* y_dev) {
+  static std::mutex mu;
+  static void* scratch_addr[kNoAllocMaxDevices] = {nullptr};
+  if (!c) return RSN_EINVAL;
+  if (n_rhs < 0 || (n_rhs > 0 && (!E || !x_dev || !y_dev))) RSN_FAIL(c, RSN_EINVAL, "bad arguments");
+  if (precision != RSN_FP64 && precision != RSN_MIXED) RSN_FAIL(c, RSN_EINVAL, "bad precision");
+  if (!c->has_grid || !c->has_v || !c->has_cap || c->dirty || !c->jd.p)
+    RSN_FAIL(c, RSN_ESTATE,
+             "rsn_apply_noalloc: the operator data is not on the device yet; an allocating call "
+             "(e.g. rsn_apply) after the last setter uploads it");
+  if (n_rhs == 0) return RSN_OK;
+  // scratch layout: [BatchDev | E | voff | junc | projector coefficients]
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t o_E = up(sizeof(BatchDev));
+  const size_t o_voff = up(o_E + (size_t)n_rhs * sizeof(double));
+  const size_t o_junc = up(o_voff + (size_t)n_rhs * sizeof(long long));
+  const size_t o_c = up(o_junc + (size_t)n_rhs * sizeof(int));
+  const size_t need = o_c + (size_t)n_rhs * std::max(1, c->n_proj) * sizeof(double2);
+  if (need > kNoAllocScratchBytes)
+    RSN_FAIL(c, RSN_EINVAL,
+             "rsn_apply_noalloc: %d vectors with %d projectors need %zu bytes of scratch, more than the %zu-byte "
+             "fixed array; split the call",
+             n_rhs, c->n_proj, need, kNoAllocScratchBytes);
+  if (c->device < 0 || c->device >= kNoAllocMaxDevices) RSN_FAIL(c, RSN_EINVAL, "device index too large");
+  rsn_status rs = enter(c);  // makes the context's device current
+  if (rs != RSN_OK) return rs;
+  unsigned char* base;
+  {
+    // first call on a device: host code needs the device address of the array
+    std::lock_guard<std::mutex> lock(mu);
+    if (!scratch_addr[c->device]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) RSN_FAIL(c, RSN_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      scratch_addr[c->device] = p;
+    }
+    base = static_cast<unsigned char*>(scratch_addr[c->device]);
+  }
+  const bool fp32 = precision == RSN_MIXED;
+  BatchDev b;
+  memset(&b, 0, sizeof(b));
+  b.nslots = n_rhs;
+  b.E = reinterpret_cast<double*>(base + o_E);
+  b.voff = reinterpret_cast<long long*>(base + o_voff);
+  b.junc = reinterpret_cast<int*>(base + o_junc);
+  void* cbuf = base + o_c;
+  const BatchDev* bdev = reinterpret_cast<const BatchDev*>(base);
+  RSN_CUDA(c, cudaMemcpyAsync(base, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));
+  RSN_CUDA(c, cudaMemcpyAsync(b.E, E, n_rhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  noalloc_tables_kernel<<<(n_rhs + 255) / 256, 256, 0, c->st>>>(n_rhs, c->N, b.voff, b.junc);
+  RSN_CUDA(c, cudaGetLastError());
+  LaunchCfg cfg;
+  if ((rs = make_cfg(c, fp32, n_rhs, cfg)) != RSN_OK) return rs;
+  const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs);
+  if (c->n_proj > 0)
+    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
+  if (t.tma && (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0) {
+    RSN_CUDA(c, launch_op_tma(OP_APPLY, fp32, c->R, dim3(cfg.inner.n, n_rhs), t.threads, t.smem, c->st,
+                              cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
+  } else {
+    const size_t smem = op_smem_bytes(fp32, OP_APPLY, c->R, t.TY, c->nx, c->n_proj);
+    const int threads = ((c->nx * t.TY + t.ppt - 1) / t.ppt + 31) / 32 * 32;
+    RSN_CUDA(c, launch_op(OP_APPLY, fp32, c->R, t.ppt, dim3(cfg.inner.n, n_rhs), threads, smem, c->st,
+                          cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
+  }
+  return leave(c);
+}
