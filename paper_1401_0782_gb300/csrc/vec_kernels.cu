@@ -277,7 +277,13 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
       // a true residual that did not improve 4x on the previous one
       const bool no_gain = st == SL_CHECK && nrm > 0.0625 * b.rlast2[s];
       const int stall = no_gain ? b.stall[s] + 1 : 0;
-      const bool stalled = b.stall_cap > 0 && stall >= b.stall_cap;
+      // precision-limited systems are handed back early: either the true
+      // residual stopped improving, or its rate so far (log rel per
+      // iteration) predicts more iterations than the budget allows
+      const int tot = b.total_iters[s];
+      const bool slow = st == SL_CHECK && tot >= 400 &&
+                        (rel >= 1.0 || (double)tot * log(b.tol) / log(rel) > (double)b.max_iter);
+      const bool stalled = b.stall_cap > 0 && (stall >= b.stall_cap || slow);
       const bool fail = !isfinite(rel) || b.total_iters[s] >= b.max_iter || b.n_upd[s] >= b.max_upd || stalled;
       if (conv || fail) {
         b.out_iters[sy] = b.total_iters[s];
