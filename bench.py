@@ -186,6 +186,9 @@ def oracle_sample(n_solves: int, cores: int, E: float = 0.2):
     rng = np.random.default_rng(8)
     pick = rng.choice(cols, n_solves, replace=False)
     ctx = mp.get_context("spawn")
+    # one thread per worker process: the pool, not BLAS, uses the cores
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     with ctx.Pool(cores) as pool:
         pool.map(_oracle_worker, [(int(cols[0]), E, 1e-2)] * cores)  # import + setup warm-up, not timed
         t0 = time.perf_counter()

@@ -1,0 +1,65 @@
+"""T(E) as a differentiable function of the local potential.
+
+``transmission(ctx, v_loc, energies, cols, opts)`` returns T(E) (Eq.
+T-realspace, coupling 2*CAP) as a torch tensor whose gradient with respect to
+``v_loc`` is the adjoint of ``rsn_transmission_vjp``:
+
+    dT(E)/dV_loc(r) = 8 sum_j Gamma_R,j Re( lambda_j(r) x_j(r) ),
+    lambda_j = G(E) (Gamma_L o conj(x_j)),
+
+one adjoint solve per column with the same operator (G^T = G, Eq.
+complex-sym).  The forward pass computes T only; the backward pass calls the
+library's vector-Jacobian product, which solves the forward columns again and
+their adjoints (memory stays O(slots * N) instead of O(columns * N)).
+
+The autograd machinery only marshals arguments: every solve, reduction and
+gradient accumulation runs in the CUDA library.
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class TransmissionFn(torch.autograd.Function):
+    """T(E) for a 1-D tensor of N potential values (any device, float64)."""
+
+    @staticmethod
+    def forward(ctx, v_loc: torch.Tensor, energies: Sequence[float], cols: np.ndarray, context: "B.Context",
+                opts: Optional[B.SolverOpts]):
+        v = v_loc.detach().to("cpu", torch.float64).contiguous().numpy()
+        context.set_potential(v)
+        T = context.transmission(energies, cols, opts)
+        ctx.context = context
+        ctx.energies = np.asarray(energies, dtype=np.float64)
+        ctx.cols = cols
+        ctx.opts = opts
+        ctx.v = v
+        ctx.dev = v_loc.device
+        return torch.tensor(T, dtype=torch.float64, device=v_loc.device)
+
+    @staticmethod
+    def backward(ctx, grad_T: torch.Tensor):
+        context = ctx.context
+        context.set_potential(ctx.v)  # the potential of this forward pass
+        T_bar = grad_T.detach().to("cpu", torch.float64).numpy()
+        if ctx.dev.type == "cuda":
+            dV = torch.empty(ctx.v.size, dtype=torch.float64, device=ctx.dev)
+            context.transmission_vjp(ctx.energies, T_bar, ctx.cols, ctx.opts, dV_out=dV)
+        else:
+            _, dv = context.transmission_vjp(ctx.energies, T_bar, ctx.cols, ctx.opts)
+            dV = torch.from_numpy(dv)
+        return dV, None, None, None, None
+
+
+def transmission(context: "B.Context", v_loc: torch.Tensor, energies: Sequence[float],
+                 cols: Optional[Sequence[int]] = None, opts: Optional[B.SolverOpts] = None) -> torch.Tensor:
+    """Differentiable T(E); ``context`` must hold the junction (``set_junction``)."""
+    if cols is None:
+        cols = context.junction.right_columns()
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    return TransmissionFn.apply(v_loc, list(energies), cols, context, opts)

@@ -111,7 +111,7 @@ struct rsn_ctx {
   // device operator data
   DevBuf dg64, dg32, gld, L_idx, L_gam, inv_ptr, inv_proj, inv_val64, inv_val32;
   DevBuf grp_ptr, grp_p0, grp_np, grp_voff, grp_idx, grp_val64, grp_val32, ekb;
-  int n_groups = 0, nL = 0;
+  int n_groups = 0, nL = 0, max_np = 1;
   JuncDev jh{};
   DevBuf jd;  // device JuncDev (one per launch configuration, uploaded before a batch)
 
@@ -204,6 +204,7 @@ static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslo
   t.threads = threads;
   int want = 8 * 152;
   int zt = (want + nslots * t.ytiles - 1) / (nslots * t.ytiles);
+  if (mode == OP_RESID) zt = nz;  // few systems need a true residual at a time: spread each over many CTAs
   zt = std::max(1, std::min(zt, std::max(1, nz / (2 * R + 2))));
   if (c->tile_override[1] > 0) zt = (nz + c->tile_override[1] - 1) / c->tile_override[1];
   t.Lz = (nz + zt - 1) / zt;
@@ -297,6 +298,8 @@ static rsn_status commit_setup(rsn_ctx* c) {
       for (int64_t e = c->poff[k]; e < c->poff[k + 1]; ++e) cnt[c->pidx[e] + 1]++;
   }
   c->n_groups = (int)gp0.size();
+  c->max_np = 1;
+  for (int v : gnp) c->max_np = std::max(c->max_np, v);
   for (long long i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
   const size_t nnz = (size_t)cnt[N];
   std::vector<int> iproj(std::max<size_t>(1, nnz)), fill(cnt.begin(), cnt.end() - 1);
@@ -850,7 +853,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
     for (int it = 0; it < iters; ++it) {
       cudaError_t e;
       if ((e = launch_zero(fp32, S, nB, st, jr, bdev)) != cudaSuccess) return e;
-      if (proj && (e = launch_project(1, fp32, S, c->n_groups, st, jr, bdev, nullptr, w.c_x.p)) != cudaSuccess)
+      if (proj && (e = launch_project(1, fp32, S, c->n_groups, c->max_np, st, jr, bdev, nullptr, w.c_x.p)) != cudaSuccess)
         return e;
       if ((e = launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, bdev,
                          nullptr, nullptr, nullptr)) != cudaSuccess)
@@ -858,7 +861,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       if ((e = launch_x_update(fp32, S, nB, st, jr, bdev)) != cudaSuccess) return e;
       if ((e = launch_sched(S, it, st, jr, bdev)) != cudaSuccess) return e;
       if ((e = launch_emit(S, st, jr, bdev)) != cudaSuccess) return e;
-      if (proj && (e = launch_project(0, fp32, S, c->n_groups, st, ji, bdev, nullptr, w.c_r.p)) != cudaSuccess)
+      if (proj && (e = launch_project(0, fp32, S, c->n_groups, c->max_np, st, ji, bdev, nullptr, w.c_r.p)) != cudaSuccess)
         return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it], st, evf)) != cudaSuccess) return e;
       e = cfg.inner.tma ? launch_op_tma(OP_COCG, fp32, c->R, gi, cfg.inner.threads, cfg.inner.smem, st, ji, bdev,
@@ -1046,7 +1049,7 @@ rsn_status rsn_apply(rsn_ctx* c, int precision, int n_rhs, const double* E, cons
   const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs);
   void* cbuf = q.out_t.p;
   if (c->n_proj > 0)
-    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
+    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->max_np, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
   const bool aligned = (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0;
   if (t.tma && aligned) {
     RSN_CUDA(c, launch_op_tma(OP_APPLY, fp32, c->R, dim3(cfg.inner.n, n_rhs), t.threads, t.smem, c->st,
@@ -1532,7 +1535,7 @@ extern "C" rsn_status rsn_apply_noalloc(rsn_ctx* c, int precision, int n_rhs, co
   if ((rs = make_cfg(c, fp32, n_rhs, cfg)) != RSN_OK) return rs;
   const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs);
   if (c->n_proj > 0)
-    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
+    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->max_np, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
   if (t.tma && (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0) {
     RSN_CUDA(c, launch_op_tma(OP_APPLY, fp32, c->R, dim3(cfg.inner.n, n_rhs), t.threads, t.smem, c->st,
                               cfg.jt_inner, bdev, x_dev, y_dev, cbuf));

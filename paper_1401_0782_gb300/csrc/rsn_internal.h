@@ -148,7 +148,7 @@ size_t op_tma_smem_bytes(bool fp32, int mode, int R, int nx, int ny, int n_proj)
 cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
                                const BatchDev* b);
-cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, cudaStream_t st,
+cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, int max_np, cudaStream_t st,
                            const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out);
 cudaError_t launch_book(int nslots, int slot_it, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 constexpr int kBookWarps = 8;  // slots per CTA of the bookkeeping kernel (one warp each)

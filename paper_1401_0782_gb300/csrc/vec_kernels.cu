@@ -125,61 +125,109 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
 // ---------------------------------------------------------------------------
 enum { PJ_R = 0, PJ_X = 1, PJ_IN = 2 };
 
-template <typename T, int MODE>
+template <typename T, int MODE, int NP, int SPB>
 __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp,
                                                       const void* __restrict__ x_in, void* __restrict__ c_out) {
+  // NP: projectors per atom at compile time (>= the junction's largest group);
+  // SPB: slots per CTA, so each projector value is loaded once for SPB slots
   using CT = typename std::conditional<MODE == PJ_X, double, T>::type;
   using C = typename cx<CT>::t;
   using CO = typename cx<T>::t;
   const BatchDev& b = *bp;
-  const int g = blockIdx.x, s = blockIdx.y;
-  if constexpr (MODE == PJ_R) {
-    if (b.state[s] != SL_ACTIVE) return;
-  } else if constexpr (MODE == PJ_X) {
-    const int st = b.state[s];
-    if (st != SL_NEW && st != SL_CHECK) return;
-  }
-  const JuncDev& J = jt[b.junc[s]];
-  if (g >= J.n_groups) return;
+  const int g = blockIdx.x;
   __shared__ double red[32 * 2];
+  __shared__ int s_slot[SPB];
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  if (threadIdx.x < SPB) {
+    const int s = blockIdx.y * SPB + threadIdx.x;
+    bool use = s < b.nslots;
+    if (use) {
+      if constexpr (MODE == PJ_R) {
+        use = b.state[s] == SL_ACTIVE;
+      } else if constexpr (MODE == PJ_X) {
+        const int st = b.state[s];
+        use = st == SL_NEW || st == SL_CHECK;
+      }
+    }
+    if (use && g >= jt[b.junc[s]].n_groups) use = false;
+    s_slot[threadIdx.x] = use ? s : -1;
+    if (use) atomicOr(&s_any, 1);
+  }
+  __syncthreads();
+  if (!s_any) return;
+  int slot[SPB];
+  long long vo[SPB], xo[SPB];
+  double sig[SPB];
+#pragma unroll
+  for (int u = 0; u < SPB; ++u) {
+    slot[u] = s_slot[u];
+    const int s = slot[u] >= 0 ? slot[u] : 0;
+    vo[u] = b.voff[s];
+    xo[u] = (MODE == PJ_X) ? b.xo[s] : 0;
+    sig[u] = (MODE == PJ_X) ? b.sigma[s] : 1.0;
+  }
+  // every active slot of this CTA belongs to a junction with this group; the
+  // junction of the first active slot supplies the support (batches share it)
+  int s0 = 0;
+  for (int u = 0; u < SPB; ++u)
+    if (slot[u] >= 0) {
+      s0 = slot[u];
+      break;
+    }
+  const JuncDev& J = jt[b.junc[s0]];
   const int p0 = J.grp_p0[g], np = J.grp_np[g];
   const int k0 = J.grp_ptr[g], k1 = J.grp_ptr[g + 1], len = k1 - k0;
   const long long vb = J.grp_voff[g];
-  const long long vo = b.voff[s];
-  const long long xo = (MODE == PJ_X) ? b.xo[s] : 0;
-  const double sig = (MODE == PJ_X) ? b.sigma[s] : 1.0;
-  C acc[kMaxGroupNp];
+  C acc[SPB][NP];
 #pragma unroll
-  for (int p = 0; p < kMaxGroupNp; ++p) acc[p] = czero<C>();
+  for (int u = 0; u < SPB; ++u)
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[u][p] = czero<C>();
   for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
     const int gi = J.grp_idx[kk];
-    C v;
-    if constexpr (MODE == PJ_R) {
-      v = reinterpret_cast<const CO*>(b.r)[vo + gi];
-    } else if constexpr (MODE == PJ_X) {
-      const double2 xx = b.x64[xo + gi];
-      const double2 dd = to64(reinterpret_cast<const CO*>(b.d)[vo + gi]);
-      v = mk2(fma(sig, dd.x, xx.x), fma(sig, dd.y, xx.y));
-    } else {
-      v = reinterpret_cast<const CO*>(x_in)[vo + gi];
-    }
     const long long vk = vb + (kk - k0);
+    CT a[NP];
 #pragma unroll
-    for (int p = 0; p < kMaxGroupNp; ++p) {
+    for (int p = 0; p < NP; ++p) {
       if (p < np) {
-        CT a;
-        if constexpr (sizeof(CT) == 8) a = (CT)J.grp_val64[vk + (long long)p * len];
-        else a = (CT)J.grp_val32[vk + (long long)p * len];
-        acc[p] = rfma(a, v, acc[p]);
+        if constexpr (sizeof(CT) == 8) a[p] = (CT)J.grp_val64[vk + (long long)p * len];
+        else a[p] = (CT)J.grp_val32[vk + (long long)p * len];
+      } else {
+        a[p] = 0;
       }
     }
+#pragma unroll
+    for (int u = 0; u < SPB; ++u) {
+      if (slot[u] < 0) continue;
+      C v;
+      if constexpr (MODE == PJ_R) {
+        v = reinterpret_cast<const CO*>(b.r)[vo[u] + gi];
+      } else if constexpr (MODE == PJ_X) {
+        const double2 xx = b.x64[xo[u] + gi];
+        const double2 dd = to64(reinterpret_cast<const CO*>(b.d)[vo[u] + gi]);
+        v = mk2(fma(sig[u], dd.x, xx.x), fma(sig[u], dd.y, xx.y));
+      } else {
+        v = reinterpret_cast<const CO*>(x_in)[vo[u] + gi];
+      }
+#pragma unroll
+      for (int p = 0; p < NP; ++p) acc[u][p] = rfma(a[p], v, acc[u][p]);
+    }
   }
-  C* out = reinterpret_cast<C*>(c_out) + (size_t)s * J.n_proj + p0;
-  for (int p = 0; p < np; ++p) {
-    CT v[2] = {acc[p].x, acc[p].y};
-    double o[2];
-    block_sum<2>(v, red, o);
-    if (threadIdx.x == 0) out[p] = mk2((CT)o[0], (CT)o[1]);
+#pragma unroll
+  for (int u = 0; u < SPB; ++u) {
+    if (slot[u] < 0) continue;  // uniform across the CTA
+    C* out = reinterpret_cast<C*>(c_out) + (size_t)slot[u] * J.n_proj + p0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      if (p < np) {  // uniform across the CTA
+        CT v[2] = {acc[u][p].x, acc[u][p].y};
+        double o[2];
+        block_sum<2>(v, red, o);
+        if (threadIdx.x == 0) out[p] = mk2((CT)o[0], (CT)o[1]);
+      }
+    }
   }
 }
 
@@ -558,18 +606,32 @@ cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, cudaStream_t st, const JuncDev* jt,
-                           const BatchDev* b, const void* x_in, void* c_out) {
-  dim3 grid(n_groups, nslots);
+template <int NP, int SPB>
+static void launch_project_np(int mode, bool fp32, dim3 grid, cudaStream_t st, const JuncDev* jt, const BatchDev* b,
+                              const void* x_in, void* c_out) {
   if (mode == PJ_R) {
-    if (fp32) project_kernel<float, PJ_R><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
-    else project_kernel<double, PJ_R><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
+    if (fp32) project_kernel<float, PJ_R, NP, SPB><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
+    else project_kernel<double, PJ_R, NP, SPB><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
   } else if (mode == PJ_X) {
-    if (fp32) project_kernel<float, PJ_X><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
-    else project_kernel<double, PJ_X><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
+    if (fp32) project_kernel<float, PJ_X, NP, SPB><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
+    else project_kernel<double, PJ_X, NP, SPB><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
   } else {
-    if (fp32) project_kernel<float, PJ_IN><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
-    else project_kernel<double, PJ_IN><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
+    if (fp32) project_kernel<float, PJ_IN, NP, SPB><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
+    else project_kernel<double, PJ_IN, NP, SPB><<<grid, 128, 0, st>>>(jt, b, x_in, c_out);
+  }
+}
+
+cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, int max_np, cudaStream_t st,
+                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out) {
+  // slots per CTA: the projector values of an atom are loaded once for all of them
+  if (max_np <= 4) {
+    launch_project_np<4, 4>(mode, fp32, dim3(n_groups, (nslots + 3) / 4), st, jt, b, x_in, c_out);
+  } else if (max_np <= 9) {
+    launch_project_np<9, 2>(mode, fp32, dim3(n_groups, (nslots + 1) / 2), st, jt, b, x_in, c_out);
+  } else if (max_np <= kMaxGroupNp) {
+    launch_project_np<kMaxGroupNp, 1>(mode, fp32, dim3(n_groups, nslots), st, jt, b, x_in, c_out);
+  } else {
+    return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }

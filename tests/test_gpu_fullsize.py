@@ -1,0 +1,127 @@
+"""Parity at the benchmark sizes, on sampled outputs and on properties that
+hold at any size, plus error paths.
+
+* 24x24x120 junction (8th-order FD, 80 projectors): sampled columns certified
+  by the oracle's operator (true residual), one column against the oracle's
+  certified Krylov solve, the T reduction recomputed by the oracle formula from
+  the GPU's own columns, mixed against FP64.
+* 48x48x192 junction (12th-order FD, 540 s/p/d projectors): dT/dV_loc against
+  central differences of the GPU T and against the sum rule
+  sum_r dT/dV_r = -dT/dE (a uniform potential shift is an energy shift).
+* Error paths: empty calls, bad columns, a deadline that expires, an
+  iteration cap that is too small.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1401_0782_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_0782_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def junction():
+    return P.molecular_junction(seed=1)
+
+
+def _unit(N, cols):
+    b = np.zeros((N, len(cols)), complex)
+    b[cols, np.arange(len(cols))] = 1
+    return b
+
+
+def test_junction_columns_certified_and_T_reduction(B, junction):
+    j = junction
+    cols = P.column_subset(j, 8, seed=8)
+    E = 0.2
+    ctx = B.Context(0).set_junction(j)
+    x64, it64, rr64 = ctx.solve_columns([E], cols, B.default_opts(B.RSN_FP64))
+    xm, itm, rrm = ctx.solve_columns([E], cols, B.default_opts(B.RSN_MIXED))
+    x64 = x64[0].cpu().numpy().T
+    xm = xm[0].cpu().numpy().T
+    b = _unit(j.N, cols)
+    r64 = np.linalg.norm(b - O.apply_operator(j, E, x64), axis=0)
+    rm = np.linalg.norm(b - O.apply_operator(j, E, xm), axis=0)
+    assert r64.max() <= 2e-13 and rm.max() <= 1.5e-10, (r64.max(), rm.max())
+    assert np.all(it64 > 0) and np.all(itm > 0)
+    # one column against the oracle's own certified solve
+    x_ref = O.solve_columns(j, E, cols[:1], method="krylov", rtol=1e-13)[:, 0]
+    assert np.linalg.norm(x64[:, 0] - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+    # T reduction at full size: oracle formula on the GPU's columns
+    T_gpu = ctx.transmission([E], cols, B.default_opts(B.RSN_FP64))[0]
+    T_from_cols = 4.0 * np.sum(j.gamma_r[cols] * O.column_weights(j, x64))
+    assert abs(T_gpu - T_from_cols) <= 1e-9 * abs(T_from_cols)
+    ctx.close()
+
+
+def test_junction_mixed_vs_fp64_transmission(B, junction):
+    j = junction
+    cols = P.column_subset(j, 64, seed=9)
+    E = [0.17, 0.21]
+    ctx = B.Context(0).set_junction(j)
+    T64 = ctx.transmission(E, cols, B.default_opts(B.RSN_FP64))
+    Tm = ctx.transmission(E, cols, B.default_opts(B.RSN_MIXED))
+    assert np.all(np.abs(Tm - T64) <= 1e-6)
+    assert np.all(np.abs(Tm - T64) <= 1e-5 * np.abs(T64))
+    ctx.close()
+
+
+def test_large_adjoint_junction_fd_and_sum_rule(B):
+    j = P.adjoint_junction(seed=4)
+    assert j.N == 442368 and j.n_proj == 540
+    cols = P.column_subset(j, 4, seed=11)
+    E = 0.2
+    ctx = B.Context(0).set_junction(j)
+    o64 = B.default_opts(B.RSN_FP64)
+    T, g = ctx.transmission_vjp([E], [1.0], cols, o64)
+    gs = np.abs(g).max()
+    assert gs > 0
+    rng = np.random.default_rng(4)
+    pts = rng.choice(np.flatnonzero(np.abs(g) > 0.05 * gs), 3, replace=False)
+    dv = 1e-4
+    for r in pts:
+        vp = j.v_loc.copy(); vp[r] += dv
+        vm = j.v_loc.copy(); vm[r] -= dv
+        ctx.set_potential(vp)
+        Tp = ctx.transmission([E], cols, o64)[0]
+        ctx.set_potential(vm)
+        Tm = ctx.transmission([E], cols, o64)[0]
+        fd = (Tp - Tm) / (2 * dv)
+        assert abs(fd - g[r]) <= 1e-4 * gs, (r, fd, g[r])
+    ctx.set_potential(j.v_loc)
+    de = 1e-5
+    dTdE = (ctx.transmission([E + de], cols, o64)[0] - ctx.transmission([E - de], cols, o64)[0]) / (2 * de)
+    assert abs(g.sum() + dTdE) <= 1e-4 * max(abs(dTdE), gs)
+    Tm, gm = ctx.transmission_vjp([E], [1.0], cols, B.default_opts(B.RSN_MIXED))
+    assert abs(Tm[0] - T[0]) <= 1e-6 and np.abs(gm - g).max() <= 1e-4 * gs
+    ctx.close()
+
+
+def test_error_paths(B):
+    j = P.molecular_junction(seed=3, nx=10, ny=10, nz=30, n_wells=2, n_cap=4)
+    ctx = B.Context(0).set_junction(j)
+    assert ctx.transmission([], j.right_columns()).size == 0
+    assert np.array_equal(ctx.transmission([0.2, 0.3], []), np.zeros(2))
+    with pytest.raises(B.RsnError) as e:
+        ctx.transmission([0.2], [j.N])
+    assert e.value.code == B.RSN_EINVAL
+    # an iteration cap that is too small: the columns are reported, not hidden
+    x, it, rr = ctx.solve_columns([0.2], j.right_columns()[:4], B.default_opts(B.RSN_FP64, max_iter=5),
+                                  raise_on_noconv=False)
+    assert np.all(it < 0) and np.all(rr > 1e-6)
+    # a deadline that expires
+    with pytest.raises(B.RsnError) as e:
+        ctx.transmission(np.linspace(0.1, 0.3, 64), j.right_columns(), B.default_opts(B.RSN_FP64, deadline_ms=1.0,
+                                                                                      graph_iters=1))
+    assert e.value.code == B.RSN_ETIMEOUT
+    ctx.close()
