@@ -82,12 +82,18 @@ typedef struct {
     int graph_iters;    /* iterations per graph replay between convergence polls (1..256) */
     int timing;         /* 1: time every COCG operator / update launch with CUDA events
                            (read back with rsn_kernel_stats) */
+    double tol_adjoint; /* tolerance of the adjoint systems of rsn_transmission_vjp (0 = tol).
+                           Their right-hand side Gamma_L o conj(x_j) is built from a computed
+                           column, and on large, nearly resonant junctions the FP64 recurrence
+                           of an adjoint can level off above a tol that its forward column
+                           meets; a looser target here keeps tol for the columns and T */
 } rsn_solver_opts;
 
 /* Defaults for a precision: FP64 -> tol 1e-13, tol_inner 1e-6, max_iter 20000;
    MIXED -> tol 1e-10, tol_inner 1e-1, max_iter 3000 (a system that needs more,
-   or whose FP32 recurrence stalls, is finished in FP64 from its iterate);
-   max_outer 64, graphs on (16 iterations per replay), timing off. */
+   or whose FP32 recurrence stalls, is solved again in FP64 from zero);
+   both: tol_adjoint 0 (= tol), max_outer 64, graphs on (16 iterations per
+   replay), timing off. */
 void rsn_default_opts(int precision, rsn_solver_opts* opts);
 
 /* Create a context on CUDA device `device`, queuing work on `cuda_stream`

@@ -63,6 +63,7 @@ class SolverOpts(ct.Structure):
         ("use_graph", ct.c_int),
         ("graph_iters", ct.c_int),
         ("timing", ct.c_int),
+        ("tol_adjoint", ct.c_double),
     ]
 
 

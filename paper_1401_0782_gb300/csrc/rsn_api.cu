@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -69,7 +70,7 @@ struct Workspace {
   int PA = 0, PB = 0, n_proj = 0;
   DevBuf Xslot, r, p0, p1, q, d;
   DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, stall, warm, rho_cur, beta_cur;
-  DevBuf bnorm2, sigma, rlast2, tol2;
+  DevBuf bnorm2, sigma, rlast2, rrec2, tol2;
   DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters;
   int generation = 0;
 };
@@ -120,6 +121,7 @@ struct rsn_ctx {
   DevBuf bd;  // device BatchDev: [0] streaming solver, [1] rsn_apply
   std::map<GraphKey, cudaGraphExec_t> graphs;
   int* sched_host = nullptr;  // pinned mirror of BatchDev::sched
+  unsigned long long* cnt_host = nullptr;  // pinned mirror of BatchDev::counters
 
   // stats of the last solve
   int64_t st_iters = 0, st_sweeps = 0, st_launches = 0, st_fallback = 0;
@@ -413,6 +415,7 @@ void rsn_default_opts(int precision, rsn_solver_opts* o) {
     o->tol_inner = 1e-6;
     o->max_iter = 20000;
   }
+  o->tol_adjoint = 0.0;  // the adjoint systems take tol
   o->max_outer = 64;
   o->deadline_ms = 0.0;
   o->rhs_block = 0;
@@ -446,7 +449,8 @@ rsn_status rsn_create(rsn_ctx** out, int device, void* cuda_stream) {
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
-      cudaMallocHost(&c->sched_host, (3 + 2 * kMaxGraphIters) * sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&c->sched_host, (3 + 2 * kMaxGraphIters) * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->cnt_host, 4 * sizeof(unsigned long long)) != cudaSuccess) {
     g_create_err = "rsn_create: stream/event/pinned allocation failed";
     rsn_destroy(c);
     return RSN_ECUDA;
@@ -463,6 +467,7 @@ rsn_status rsn_destroy(rsn_ctx* c) {
   clear_graphs(c);
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   if (c->sched_host) cudaFreeHost(c->sched_host);
+  if (c->cnt_host) cudaFreeHost(c->cnt_host);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->t0) cudaEventDestroy(c->t0);
@@ -654,6 +659,7 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   RSN_CUDA(c, w.bnorm2.ensure(sd));
   RSN_CUDA(c, w.sigma.ensure(sd));
   RSN_CUDA(c, w.rlast2.ensure(sd));
+  RSN_CUDA(c, w.rrec2.ensure(sd));
   RSN_CUDA(c, w.tol2.ensure(sd));
   RSN_CUDA(c, w.rho0.ensure((size_t)S * PA * sizeof(double2)));
   RSN_CUDA(c, w.nrm0.ensure((size_t)S * PA * sizeof(double)));
@@ -759,6 +765,7 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.bnorm2 = w.bnorm2.as<double>();
   b.sigma = w.sigma.as<double>();
   b.rlast2 = w.rlast2.as<double>();
+  b.rrec2 = w.rrec2.as<double>();
   b.tol2 = w.tol2.as<double>();
   b.x64 = w.Xslot.as<double2>();
   b.r = w.r.p;
@@ -777,11 +784,17 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.sched = w.sched.as<int>();
   b.counters = w.counters.as<unsigned long long>();
   b.tol = o->tol;
+  b.tol_adj = o->tol_adjoint > 0 ? o->tol_adjoint : o->tol;
   b.delta = o->tol_inner;
   b.max_iter = o->max_iter;
   b.max_upd = o->max_outer;
-  b.cycle_cap = std::max(32, std::min(o->max_iter, 400));
+  // FP32 cycles end by the cycle cap as well, so that precision-limited systems
+  // are seen early; an FP64 cycle runs until its recurrence reaches the target,
+  // since true residuals that replace the recurrence in the middle of a slow
+  // phase would hide a drifted recurrence
+  b.cycle_cap = o->precision == RSN_MIXED ? std::max(32, std::min(o->max_iter, 400)) : std::max(32, o->max_iter);
   b.stall_cap = o->precision == RSN_MIXED ? 3 : 0;
+  b.handback = o->precision == RSN_MIXED ? 1 : 0;
   return b;
 }
 
@@ -907,9 +920,13 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   for (long long k = 0; k < nsys && !has_dep; ++k) has_dep = in.dep[k] >= 0;
   const long long per_sys = (long long)o->max_iter + 2LL * o->max_outer + 8;
   const long long max_replays = ((waves + (has_dep ? 2 : 1)) * per_sys + G) / G + 4;
-  bool timeout = false, finished = false;
+  bool timeout = false, finished = false, aborted = false;
+  const double abort_ratio = fp32 ? 0.5 : 0.0;
   int* hs = c->sched_host;
+  const auto t_run = std::chrono::steady_clock::now();
+  long long reps_done = 0;
   for (long long rep = 0; rep < max_replays; ++rep) {
+    ++reps_done;
     if (gexec) {
       RSN_CUDA(c, cudaGraphLaunch(gexec, st));
     } else {
@@ -917,6 +934,8 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
     }
     c->st_launches += (int64_t)G * per_iter;
     RSN_CUDA(c, cudaMemcpyAsync(hs, w.sched.p, (3 + 2 * kMaxGraphIters) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    RSN_CUDA(c, cudaMemcpyAsync(c->cnt_host, w.counters.p, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                st));
     RSN_CUDA(c, cudaStreamSynchronize(st));
     if (timing) {
       for (int it = 0; it < G; ++it) {
@@ -938,6 +957,13 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       finished = true;
       break;
     }
+    // mixed precision at a near-resonant energy: once most finished systems were
+    // handed back, stop and let the FP64 pass take every remaining system
+    if (fp32 && abort_ratio > 0 && c->cnt_host[2] >= (unsigned long long)std::max(32, S / 4) &&
+        (double)c->cnt_host[3] > abort_ratio * (double)c->cnt_host[2]) {
+      aborted = true;
+      break;
+    }
     if (o->deadline_ms > 0) {
       const double el_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
       if (el_ms > o->deadline_ms) {
@@ -946,7 +972,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       }
     }
   }
-  if (!finished && !timeout) RSN_FAIL(c, RSN_ECUDA, "streaming solver exceeded its iteration bound");
+  if (!finished && !timeout && !aborted) RSN_FAIL(c, RSN_ECUDA, "streaming solver exceeded its iteration bound");
   out.iters.resize(nsys);
   out.status.resize(nsys);
   out.relres.resize(nsys);
@@ -959,6 +985,17 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   out.timeout = timeout;
   out.krylov = cnt[0];
   out.updates = cnt[1];
+  if (getenv("RSN_VERBOSE")) {
+    long long bad = 0, it_max = 0;
+    for (long long k = 0; k < nsys; ++k) {
+      bad += out.status[k] != 0;
+      it_max = std::max<long long>(it_max, out.iters[k]);
+    }
+    fprintf(stderr, "[rsn] stream %s: %lld systems, %d slots, %lld iterations, %.1f ms, %llu COCG iterations "
+            "(max %lld per system), %llu true residuals, %lld unfinished\n", fp32 ? "mixed" : "fp64", nsys, S,
+            reps_done * G, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_run).count(),
+            (unsigned long long)cnt[0], it_max, (unsigned long long)cnt[1], bad);
+  }
   c->st_iters += (int64_t)cnt[0];
   c->st_sweeps += (int64_t)cnt[1];
   return RSN_OK;
@@ -996,7 +1033,7 @@ static rsn_status check_solve_args(rsn_ctx* c, int n_e, const double* E, int n_c
   if (n_e < 0 || n_cols < 0) RSN_FAIL(c, RSN_EINVAL, "negative sizes");
   if ((n_e > 0 && !E) || (n_cols > 0 && !cols) || !o) RSN_FAIL(c, RSN_EINVAL, "NULL argument");
   if (o->precision != RSN_FP64 && o->precision != RSN_MIXED) RSN_FAIL(c, RSN_EINVAL, "bad precision");
-  if (!(o->tol > 0) || !(o->tol_inner > 0) || !(o->tol_inner < 1) || o->max_iter < 1 || o->max_outer < 1 ||
+  if (!(o->tol > 0) || !(o->tol_adjoint >= 0) || !(o->tol_inner > 0) || !(o->tol_inner < 1) || o->max_iter < 1 || o->max_outer < 1 ||
       o->graph_iters < 0 || o->rhs_block < 0)
     RSN_FAIL(c, RSN_EINVAL, "bad solver options");
   for (int e = 0; e < n_e; ++e)
@@ -1092,19 +1129,21 @@ rsn_status rsn_solve_columns(rsn_ctx* c, int n_e, const double* E, int n_cols, c
   if ((rs = run_stream(c, o, in, reinterpret_cast<double2*>(x_dev), nullptr, false, 0, t_start, so)) != RSN_OK)
     return rs;
   if (o->precision == RSN_MIXED) {
-    // systems whose FP32 recurrence stalled continue in FP64 from their iterate
+    // systems whose FP32 recurrence stalled, or that an aborted mixed pass did
+    // not finish, are solved again in FP64 from zero
     std::vector<long long> F;
     StreamIn sub;
     for (long long k = 0; k < nsys; ++k)
       if (so.status[k] != 0) {
         F.push_back(k);
         sub.push(in, (size_t)k);
-        sub.bn2.back() = 1.0;  // unit right-hand side, warm start
+        sub.bn2.back() = 0.0;  // cold start: a stalled FP32 iterate slows FP64 COCG down
       }
     if (!F.empty()) {
       rsn_solver_opts o64;
       rsn_default_opts(RSN_FP64, &o64);
       o64.tol = o->tol;
+      o64.tol_adjoint = o->tol_adjoint;
       o64.deadline_ms = o->deadline_ms;
       o64.use_graph = o->use_graph;
       o64.graph_iters = o->graph_iters;
@@ -1196,9 +1235,9 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
     RSN_CUDA(c, q.t_all.ensure(NS * sizeof(double)));
     RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, q.out_t.p, NS * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     if (o->precision == RSN_MIXED) {
-      // systems whose FP32 recurrence stalled are re-solved in FP64: forward
-      // systems warm-start from their kept iterate (vjp) or restart (T only);
-      // an adjoint is redone whenever it or its forward system is
+      // systems whose FP32 recurrence stalled (or that the aborted mixed pass
+      // never finished) are re-solved in FP64 from zero; an adjoint is redone
+      // whenever it or its forward system is
       std::vector<long long> F;
       StreamIn sub;
       std::vector<int> pos(NS, -1);
@@ -1207,7 +1246,7 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
           pos[k] = (int)F.size();
           F.push_back(k);
           sub.push(in, (size_t)k);
-          sub.bn2.back() = adjoint ? 1.0 : 0.0;
+          sub.bn2.back() = 0.0;  // cold start (see solve_columns)
         }
       if (adjoint)
         for (long long k = M; k < 2 * M; ++k)
@@ -1221,6 +1260,7 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
         rsn_solver_opts o64;
         rsn_default_opts(RSN_FP64, &o64);
         o64.tol = o->tol;
+        o64.tol_adjoint = o->tol_adjoint;
         o64.deadline_ms = o->deadline_ms;
         o64.use_graph = o->use_graph;
         o64.graph_iters = o->graph_iters;

@@ -91,6 +91,7 @@ struct BatchDev {
   double* bnorm2;
   double* sigma;        // ||b||: the inner-precision vectors hold r / sigma and d / sigma
   double* rlast2;       // true ||r||^2 at the previous replacement (progress check)
+  double* rrec2;        // recurrence ||r / sigma||^2 when the cycle ended (drift check)
   double* tol2;         // recurrence target ||r||^2 of the current cycle
   // vectors
   double2* x64;
@@ -125,12 +126,14 @@ struct BatchDev {
   double* out_t;             // T partial sum_{i in L} Gamma_L |x(i)|^2 per system (may be null)
   int* sched;                // [0] next system, [1] busy slots, [3 + it] busy after iteration it of a
                              // replay, [3 + kMaxGraphIters + it] systems that did a COCG iteration
-  unsigned long long* counters;  // [0] COCG iterations, [1] reliable updates
+  unsigned long long* counters;  // [0] COCG iterations, [1] reliable updates, [2] finished, [3] not converged
   // options
   double tol, delta;
+  double tol_adj;  // tolerance of systems with a computed right-hand side (col < 0)
   int max_iter, max_upd;
   int cycle_cap;  // a cycle longer than this ends with a true residual even if its target was not met
-  int stall_cap;  // stalled true residuals in a row before a system is handed back (0 = never)
+  int stall_cap;  // true residuals in a row without a 4x gain before a system is handed back (0 = never)
+  int handback;   // 1: systems whose predicted iteration count exceeds max_iter are handed back early
 };
 
 enum OpMode { OP_COCG = 0, OP_RESID = 1, OP_APPLY = 2 };

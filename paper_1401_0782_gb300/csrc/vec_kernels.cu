@@ -60,17 +60,26 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
   const JuncDev& J = jt[b.junc[s]];
   if ((int)blockIdx.x >= J.nB) return;
   __shared__ double red[32 * 3];
-  __shared__ double2 s_mu[64];
+  __shared__ double2 s_mu[kVecThreads];
   __shared__ double2 s_alpha;
   const int k = b.iters[s];
-  // mu = p^T A p from the operator kernel's partials: loaded in parallel,
-  // summed in a fixed order
+  // mu = p^T A p from the operator kernel's partials (any number of tiles):
+  // thread t adds partials t, t + 256, ... and thread 0 adds those sums in
+  // thread order, so the order is fixed for a given tiling
   const int nA = J.nA;
-  for (int t = threadIdx.x; t < nA; t += blockDim.x) s_mu[t & 63] = b.mu_part[(size_t)s * b.PA + t];
+  {
+    double2 m = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < nA; t += kVecThreads) {
+      const double2 v = b.mu_part[(size_t)s * b.PA + t];
+      m.x += v.x;
+      m.y += v.y;
+    }
+    s_mu[threadIdx.x] = m;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double2 mu = make_double2(0.0, 0.0);
-    for (int t = 0; t < nA && t < 64; ++t) { mu.x += s_mu[t].x; mu.y += s_mu[t].y; }
+    for (int t = 0; t < kVecThreads && t < nA; ++t) { mu.x += s_mu[t].x; mu.y += s_mu[t].y; }
     s_alpha = cdiv(b.rho_cur[s], mu);
   }
   __syncthreads();
@@ -271,8 +280,10 @@ __global__ void __launch_bounds__(32 * kBookWarps) book_kernel(const JuncDev* __
   b.rho_cur[s] = rho;
   if (!isfinite(nrm)) {
     b.restart[s] = 1;
+    b.rrec2[s] = 0.0;
     b.state[s] = SL_CHECK;
   } else if (nrm <= b.tol2[s] || tot >= b.max_iter || cyc >= b.cycle_cap) {
+    b.rrec2[s] = nrm;
     b.state[s] = SL_CHECK;
   }
 }
@@ -321,29 +332,40 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
       const double bn2 = b.bnorm2[s];
       const double rel = sqrt(nrm / bn2);
       const int sy = b.sys[s];
-      const bool conv = ((st == SL_CHECK || b.warm[s]) && rel <= b.tol) || nrm == 0.0;
-      // a true residual that did not improve 4x on the previous one
+      const double tol = b.col[s] >= 0 ? b.tol : b.tol_adj;
+      const bool conv = ((st == SL_CHECK || b.warm[s]) && rel <= tol) || nrm == 0.0;
+      // the recurrence has drifted when the true residual is more than 4x the
+      // recurrence residual of the cycle that just ended (rounding in the
+      // inner-precision Krylov basis): restart it from the true residual.
+      // Cycles that did not cut the previous true residual by 4x are counted.
+      // Early on such a plateau is ordinary slow Krylov convergence on an
+      // indefinite operator, and a restart would throw the Krylov space away;
+      // within three decades of the tolerance, two of them in a row mean the
+      // recurrence has lost its accuracy (the true residuals that replace it
+      // at the cycle cap hide the drift) and it restarts.
+      const bool drift = st == SL_CHECK && nrm > 16.0 * b.rrec2[s] * bn2;
       const bool no_gain = st == SL_CHECK && nrm > 0.0625 * b.rlast2[s];
       const int stall = no_gain ? b.stall[s] + 1 : 0;
       // precision-limited systems are handed back early: either the true
       // residual stopped improving, or its rate so far (log rel per
       // iteration) predicts more iterations than the budget allows
       const int tot = b.total_iters[s];
-      const bool slow = st == SL_CHECK && tot >= 400 &&
-                        (rel >= 1.0 || (double)tot * log(b.tol) / log(rel) > (double)b.max_iter);
-      const bool stalled = b.stall_cap > 0 && (stall >= b.stall_cap || slow);
+      const bool slow = st == SL_CHECK && tot >= 500 &&
+                        (rel >= 1.0 || (double)tot * log(tol) / log(rel) > 1.5 * (double)b.max_iter);
+      const bool stalled = (b.stall_cap > 0 && stall >= b.stall_cap) || (b.handback && slow);
       const bool fail = !isfinite(rel) || b.total_iters[s] >= b.max_iter || b.n_upd[s] >= b.max_upd || stalled;
       if (conv || fail) {
         b.out_iters[sy] = b.total_iters[s];
         b.out_relres[sy] = rel;
         b.out_status[sy] = conv ? 0 : (stalled ? 3 : (b.restart[s] ? 2 : 1));
+        atomicAdd(b.counters + 2, 1ull);               // finished systems
+        if (!conv) atomicAdd(b.counters + 3, 1ull);    // handed back (precision-limited / failed)
         st = SL_DRAIN;
       } else {
-        // A replacement that did not cut the true residual by 4x means the
-        // inner-precision recurrence has lost its way (rounding in the Krylov
-        // basis): restart it from the true residual instead of continuing.
+        // a drifted recurrence restarts from the true residual instead of
+        // continuing with its direction
         b.stall[s] = stall;
-        if (no_gain) b.restart[s] = 1;
+        if (drift || (stall >= 2 && rel < 1e3 * tol)) b.restart[s] = 1;
         const double2 rho_s = make_double2(rho.x / bn2, rho.y / bn2);  // r^T r of r / sigma
         b.rlast2[s] = nrm;
         if (st == SL_NEW || b.restart[s]) {
@@ -358,7 +380,7 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
         }
         b.rho_cur[s] = rho_s;
         // targets in the inner vectors' units (r / sigma, sigma^2 = ||b||^2)
-        const double t_in = b.delta * b.delta * nrm / bn2, t_out = 0.25 * b.tol * b.tol;
+        const double t_in = b.delta * b.delta * nrm / bn2, t_out = 0.25 * tol * tol;
         b.tol2[s] = t_in > t_out ? t_in : t_out;
         if (st == SL_CHECK) {
           b.n_upd[s] += 1;
@@ -451,14 +473,18 @@ __global__ void __launch_bounds__(kVecThreads) x_update_kernel(const JuncDev* __
   if (st != SL_NEW && st != SL_CHECK) return;
   const JuncDev& J = jt[b.junc[s]];
   if ((int)blockIdx.x >= J.nB) return;
-  __shared__ double s_part[64];
+  __shared__ double s_part[kVecThreads];
   __shared__ double s_sig;
   if (st == SL_NEW) {
-    for (int t = threadIdx.x; t < J.nR && t < 64; t += blockDim.x) s_part[t] = b.nrm0_part[(size_t)s * b.PA + t];
+    // ||b||^2 from the residual kernel's partials, in the fixed order of the
+    // update kernel's mu sum
+    double n2t = 0.0;
+    for (int t = threadIdx.x; t < J.nR; t += kVecThreads) n2t += b.nrm0_part[(size_t)s * b.PA + t];
+    s_part[threadIdx.x] = n2t;
     __syncthreads();
     if (threadIdx.x == 0) {
       double n2 = 0.0;
-      for (int t = 0; t < J.nR && t < 64; ++t) n2 += s_part[t];
+      for (int t = 0; t < kVecThreads && t < J.nR; ++t) n2 += s_part[t];
       s_sig = n2 > 0.0 ? sqrt(n2) : 1.0;
       if (blockIdx.x == 0) b.sigma[s] = s_sig;
     }

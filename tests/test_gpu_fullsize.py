@@ -7,7 +7,8 @@ hold at any size, plus error paths.
   the GPU's own columns, mixed against FP64.
 * 48x48x192 junction (12th-order FD, 540 s/p/d projectors): dT/dV_loc against
   central differences of the GPU T and against the sum rule
-  sum_r dT/dV_r = -dT/dE (a uniform potential shift is an energy shift).
+  sum_r dT/dV_r = -dT/dE (a uniform potential shift is an energy shift);
+  FP64 and mixed gradients agree.
 * Error paths: empty calls, bad columns, a deadline that expires, an
   iteration cap that is too small.
 """
@@ -71,8 +72,10 @@ def test_junction_mixed_vs_fp64_transmission(B, junction):
     ctx = B.Context(0).set_junction(j)
     T64 = ctx.transmission(E, cols, B.default_opts(B.RSN_FP64))
     Tm = ctx.transmission(E, cols, B.default_opts(B.RSN_MIXED))
-    assert np.all(np.abs(Tm - T64) <= 1e-6)
-    assert np.all(np.abs(Tm - T64) <= 1e-5 * np.abs(T64))
+    assert np.all(np.abs(Tm - T64) <= 1e-6)  # the mixed-mode criterion
+    # T ~ 1e-13 here (closed channels): a residual of 1e-10 of the whole vector still
+    # fixes T to a few 1e-4 of itself
+    assert np.all(np.abs(Tm - T64) <= 1e-3 * np.abs(T64))
     ctx.close()
 
 
@@ -82,7 +85,9 @@ def test_large_adjoint_junction_fd_and_sum_rule(B):
     cols = P.column_subset(j, 4, seed=11)
     E = 0.2
     ctx = B.Context(0).set_junction(j)
-    o64 = B.default_opts(B.RSN_FP64)
+    # on this junction the FP64 COCG recurrence of the adjoint systems levels off
+    # near 5e-11 (measured): they stop at 1e-10, the forward columns keep 1e-13
+    o64 = B.default_opts(B.RSN_FP64, tol_adjoint=1e-10)
     T, g = ctx.transmission_vjp([E], [1.0], cols, o64)
     gs = np.abs(g).max()
     assert gs > 0
@@ -99,7 +104,9 @@ def test_large_adjoint_junction_fd_and_sum_rule(B):
         fd = (Tp - Tm) / (2 * dv)
         assert abs(fd - g[r]) <= 1e-4 * gs, (r, fd, g[r])
     ctx.set_potential(j.v_loc)
-    de = 1e-5
+    # T(E) has a resonance of width ~3e-4 Ha here: a central difference with
+    # dE = 1e-5 carries a truncation error of ~(dE / width)^2 / 6 = 2e-4
+    de = 2e-6
     dTdE = (ctx.transmission([E + de], cols, o64)[0] - ctx.transmission([E - de], cols, o64)[0]) / (2 * de)
     assert abs(g.sum() + dTdE) <= 1e-4 * max(abs(dTdE), gs)
     Tm, gm = ctx.transmission_vjp([E], [1.0], cols, B.default_opts(B.RSN_MIXED))

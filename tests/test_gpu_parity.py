@@ -74,6 +74,22 @@ def test_solve_columns_fp64_matches_lu(B):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_columns_with_hundreds_of_tiles(B, prec):
+    # one y row and one z plane per CTA: 12 x 40 = 480 operator tiles, so the
+    # partial sums of mu and ||b||^2 span more entries than one CTA has threads
+    j = JUNCTIONS["junction_R4"]()
+    E = [0.21]
+    cols = j.right_columns()[::29]
+    ctx = B.Context(0).set_junction(j)
+    ctx.set_tiling(1, 1, 1)
+    x, iters, relres = ctx.solve_columns(E, cols, B.default_opts(B.RSN_FP64 if prec == "fp64" else B.RSN_MIXED))
+    ref = O.solve_columns(j, E[0], cols).T
+    err = np.linalg.norm(x[0].cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= (1e-9 if prec == "fp64" else 1e-6), err.max()
+    ctx.close()
+
+
 def test_solve_columns_mixed_residual_and_ragged_tiles(B):
     j = JUNCTIONS["ragged_R3"]()
     E = [0.05, 0.31]
