@@ -63,12 +63,15 @@ template <typename T> struct RawIn<T, OP_RESID> { double2 a; typename cx<T>::t b
 template <typename T> struct RawIn<T, OP_APPLY> { typename cx<T>::t a; };
 
 // At most kOpThreads threads per CTA; the minimum resident CTAs per SM bound
-// the registers per thread (64 / 85 / 128 for 1 / 2 / 3+ points per thread).
+// the registers per thread (64 / 85 / 128 for 1 / 2 / 3+ points per thread,
+// 128 for the FP64 true residual).
 constexpr int kOpThreads = 256;
+
+// One (tile, slot) of the operator: the CTA's tile blockIdx.x of slot s.
 template <typename T, int R, int PPT, int MODE>
-__global__ void __launch_bounds__(kOpThreads, (PPT == 1 ? 4 : (PPT == 2 ? 3 : 2)))
-op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const void* __restrict__ x_in,
-          void* __restrict__ y_out, const void* __restrict__ c_in) {
+__device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const BatchDev& b, const int s,
+                                        const void* __restrict__ x_in, void* __restrict__ y_out,
+                                        const void* __restrict__ c_in) {
   // compute type: FP64 for the true residual, else the inner precision
   using CT = typename std::conditional<MODE == OP_RESID, double, T>::type;
   using C = typename cx<CT>::t;   // compute complex
@@ -77,8 +80,6 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
   constexpr int Q = 2 * R + 1;
   constexpr int PF = 3;  // planes loaded ahead of use
 
-  const BatchDev& b = *bp;
-  const int s = blockIdx.y;
   if constexpr (MODE == OP_COCG) {
     if (b.state[s] != SL_ACTIVE) return;
   } else if constexpr (MODE == OP_RESID) {
@@ -350,6 +351,24 @@ op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const
       b.nrm0_part[(size_t)s * b.PA + tile] = out[0];
       b.rho0_part[(size_t)s * b.PA + tile] = make_double2(out[1], out[2]);
     }
+  }
+}
+
+template <typename T, int R, int PPT, int MODE>
+__global__ void __launch_bounds__(kOpThreads, (MODE == OP_RESID ? 2 : (PPT == 1 ? 4 : (PPT == 2 ? 3 : 2))))
+op_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const void* __restrict__ x_in,
+          void* __restrict__ y_out, const void* __restrict__ c_in) {
+  const BatchDev& b = *bp;
+  if constexpr (MODE == OP_RESID) {
+    // the true residual runs only for the NEW / CHECK slots of the list: CTA
+    // rows take its entries in turn
+    const int n = *b.lst_n;
+    for (int li = blockIdx.y; li < n; li += gridDim.y) {
+      op_tile<T, R, PPT, MODE>(jt, b, b.lst[li], x_in, y_out, c_in);
+      __syncthreads();  // the shared-memory planes are reused by the next entry
+    }
+  } else {
+    op_tile<T, R, PPT, MODE>(jt, b, blockIdx.y, x_in, y_out, c_in);
   }
 }
 

@@ -71,13 +71,14 @@ struct Workspace {
   DevBuf Xslot, r, p0, p1, q, d;
   DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, stall, warm, rho_cur, beta_cur;
   DevBuf bnorm2, sigma, rlast2, rrec2, tol2;
-  DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters;
+  DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters, lst, lst_n, fslot;
   int generation = 0;
 };
 
 // Per-call system queue and outputs.
 struct CallBufs {
-  DevBuf sys_junc, sys_E, sys_col, sys_xo, sys_xfo, sys_dep, sys_bn2, out_iters, out_relres, out_status, out_t;
+  DevBuf sys_junc, sys_E, sys_col, sys_xo, sys_xfo, sys_dep, sys_bn2, sys_started, out_iters, out_relres, out_status,
+      out_t;
   DevBuf X0, X1, wt, g, t_all, gr_cols, Td;
 };
 
@@ -618,8 +619,9 @@ static int choose_slots(rsn_ctx* c, const rsn_solver_opts* o, long long nsys, si
   const double avail = fr > reserved ? 0.6 * (double)(fr - reserved) : 0.0;
   long long cap = (long long)(avail / (double)slot_bytes(c, o->precision == RSN_MIXED));
   cap = std::max<long long>(1, std::min<long long>(cap, 8192));
-  long long want = std::max<long long>(512, std::min<long long>(2048, nsys / 4));
-  want = std::min(want, nsys);
+  // one slot per system up to 2048: a stream then ends with its slowest
+  // system instead of with a second wave of systems that waited for slots
+  const long long want = std::min<long long>(nsys, 2048);
   return (int)std::max<long long>(1, std::min(want, cap));
 }
 
@@ -672,6 +674,9 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   RSN_CUDA(c, w.c_x.ensure((size_t)S * npj * sizeof(double2)));
   RSN_CUDA(c, w.sched.ensure((3 + 2 * kMaxGraphIters) * sizeof(int)));
   RSN_CUDA(c, w.counters.ensure(4 * sizeof(unsigned long long)));
+  RSN_CUDA(c, w.lst.ensure(si));
+  RSN_CUDA(c, w.lst_n.ensure(sizeof(int)));
+  RSN_CUDA(c, w.fslot.ensure(si));
   std::vector<long long> hvo(S);
   for (int s = 0; s < S; ++s) hvo[s] = (long long)s * N;
   RSN_CUDA(c, cudaMemcpy(w.voff.p, hvo.data(), sl, cudaMemcpyHostToDevice));
@@ -697,6 +702,7 @@ static rsn_status ensure_calls(rsn_ctx* c, long long nsys) {
   RSN_CUDA(c, q.sys_xfo.ensure(n * sizeof(long long)));
   RSN_CUDA(c, q.sys_dep.ensure(n * sizeof(int)));
   RSN_CUDA(c, q.sys_bn2.ensure(n * sizeof(double)));
+  RSN_CUDA(c, q.sys_started.ensure(n * sizeof(int)));
   RSN_CUDA(c, q.out_iters.ensure(n * sizeof(int)));
   RSN_CUDA(c, q.out_relres.ensure(n * sizeof(double)));
   RSN_CUDA(c, q.out_status.ensure(n * sizeof(int)));
@@ -783,6 +789,9 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.c_x = w.c_x.as<double2>();
   b.sched = w.sched.as<int>();
   b.counters = w.counters.as<unsigned long long>();
+  b.lst = w.lst.as<int>();
+  b.lst_n = w.lst_n.as<int>();
+  b.fslot = w.fslot.as<int>();
   b.tol = o->tol;
   b.tol_adj = o->tol_adjoint > 0 ? o->tol_adjoint : o->tol;
   b.delta = o->tol_inner;
@@ -820,6 +829,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   RSN_CUDA(c, cudaMemcpyAsync(q.sys_dep.p, in.dep.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
   RSN_CUDA(c, cudaMemcpyAsync(q.sys_bn2.p, in.bn2.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, st));
   RSN_CUDA(c, cudaMemsetAsync(q.out_status.p, 0xff, nsys * sizeof(int), st));
+  RSN_CUDA(c, cudaMemsetAsync(q.sys_started.p, 0, nsys * sizeof(int), st));
   RSN_CUDA(c, cudaMemsetAsync(q.out_iters.p, 0, nsys * sizeof(int), st));
   RSN_CUDA(c, cudaMemsetAsync(q.out_relres.p, 0, nsys * sizeof(double), st));
   if (want_t) RSN_CUDA(c, cudaMemsetAsync(q.out_t.p, 0, nsys * sizeof(double), st));
@@ -839,6 +849,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   b.sys_xfo = q.sys_xfo.as<long long>();
   b.sys_dep = q.sys_dep.as<int>();
   b.sys_bn2 = q.sys_bn2.as<double>();
+  b.sys_started = q.sys_started.as<int>();
   b.out_iters = q.out_iters.as<int>();
   b.out_relres = q.out_relres.as<double>();
   b.out_status = q.out_status.as<int>();
@@ -852,7 +863,8 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   const JuncDev* jr = cfg.jt_resid;
   const int nB = c->jh.nB;
   const bool proj = c->n_proj > 0;
-  const dim3 gi(cfg.inner.n, S), gr(cfg.resid.n, S);
+  const int KL = std::min(S, kListRows);
+  const dim3 gi(cfg.inner.n, S), gr(cfg.resid.n, KL);
   const int G = std::max(1, std::min(kMaxGraphIters, o->graph_iters));
   const bool timing = o->timing != 0;
   while (timing && (int)c->tev.size() < 4 * G) {
@@ -865,13 +877,14 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
     const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     for (int it = 0; it < iters; ++it) {
       cudaError_t e;
-      if ((e = launch_zero(fp32, S, nB, st, jr, bdev)) != cudaSuccess) return e;
-      if (proj && (e = launch_project(1, fp32, S, c->n_groups, c->max_np, st, jr, bdev, nullptr, w.c_x.p)) != cudaSuccess)
+      if ((e = launch_list(st, bdev)) != cudaSuccess) return e;
+      if ((e = launch_zero(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
+      if (proj && (e = launch_project(1, fp32, KL, c->n_groups, c->max_np, st, jr, bdev, nullptr, w.c_x.p)) != cudaSuccess)
         return e;
       if ((e = launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, bdev,
                          nullptr, nullptr, nullptr)) != cudaSuccess)
         return e;
-      if ((e = launch_x_update(fp32, S, nB, st, jr, bdev)) != cudaSuccess) return e;
+      if ((e = launch_x_update(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
       if ((e = launch_sched(S, it, st, jr, bdev)) != cudaSuccess) return e;
       if ((e = launch_emit(S, st, jr, bdev)) != cudaSuccess) return e;
       if (proj && (e = launch_project(0, fp32, S, c->n_groups, c->max_np, st, ji, bdev, nullptr, w.c_r.p)) != cudaSuccess)
@@ -889,7 +902,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
     }
     return cudaSuccess;
   };
-  const int per_iter = proj ? 10 : 8;
+  const int per_iter = proj ? 11 : 9;
   const double vbytes = (double)N * (fp32 ? sizeof(float2) : sizeof(double2));
   cudaGraphExec_t gexec = nullptr;
   if (o->use_graph) {
@@ -1380,6 +1393,7 @@ static rsn_status bench_kernel_impl(rsn_ctx* c, int precision, int kind, int S, 
     return launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, dim3(cfg.resid.n, S), cfg.resid.threads, cfg.resid.smem,
                      st, cfg.jt_resid, bdev, nullptr, nullptr, nullptr);
   };
+  RSN_CUDA(c, launch_list(st, bdev));  // every slot, for the true-residual kernel
   for (int i = 0; i < 2; ++i) RSN_CUDA(c, launch());
   RSN_CUDA(c, cudaEventRecord(c->t0, st));
   for (int i = 0; i < reps; ++i) RSN_CUDA(c, launch());

@@ -21,6 +21,13 @@ constexpr int kMaxPlane = 4096; // nx*ny limit (smem plane tiles)
 constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
 constexpr int kMaxGraphIters = 256;
 constexpr int kSchedThreads = 1024;
+// CTA rows of the kernels that work only on NEW / CHECK slots (zero, true
+// residual and its projections, x update): each row takes list entries
+// row, row + kListRows, ...; a handful of slots need them per iteration
+constexpr int kListRows = 32;
+// systems past the first unstarted one that the scheduler examines for a
+// ready system (its dependency finished) when slots are free
+constexpr int kReadyWindow = 4096;
 constexpr int kVecThreads = 256;
 constexpr int kVecPerThread = 16;  // points per thread in the streaming kernels
 constexpr int kVecPts = kVecThreads * kVecPerThread;
@@ -119,6 +126,7 @@ struct BatchDev {
   const long long* sys_xfo;
   const int* sys_dep;        // system that must finish first (adjoint after forward), -1 none
   const double* sys_bn2;     // known ||b||^2 of a warm-started system (> 0: warm start), may be null
+  int* sys_started;          // 1 once a system has been given a slot
   int* out_iters;
   double* out_relres;
   int* out_status;           // -1 pending, 0 converged, 1 not converged, 2 breakdown,
@@ -127,6 +135,9 @@ struct BatchDev {
   int* sched;                // [0] next system, [1] busy slots, [3 + it] busy after iteration it of a
                              // replay, [3 + kMaxGraphIters + it] systems that did a COCG iteration
   unsigned long long* counters;  // [0] COCG iterations, [1] reliable updates, [2] finished, [3] not converged
+  int* lst;                  // NEW / CHECK slots of the current iteration, in slot order
+  int* lst_n;                // their number
+  int* fslot;                // FREE slots in slot order (scheduler scratch)
   // options
   double tol, delta;
   double tol_adj;  // tolerance of systems with a computed right-hand side (col < 0)
@@ -159,6 +170,7 @@ cudaError_t launch_sched(int nslots, int slot_it, cudaStream_t st, const JuncDev
 cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
                             const BatchDev* b);
 cudaError_t launch_emit(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
+cudaError_t launch_list(cudaStream_t st, const BatchDev* b);
 cudaError_t launch_t_final(int n_e, int n_cols, cudaStream_t st, const double* t_all,
                            const double* gr_cols, double* T_out);
 cudaError_t launch_grad_sys(int nsys, long long N, cudaStream_t st, const double2* lam, const double2* x,

@@ -22,24 +22,56 @@
 namespace rsn {
 
 // ---------------------------------------------------------------------------
-// zero x and d of newly assigned systems
+// List of the slots that need a true residual in this iteration (NEW and
+// CHECK), in slot order: one CTA, ballot + warp-count prefix per 1024 slots.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSchedThreads) list_kernel(const BatchDev* __restrict__ bp) {
+  const BatchDev& b = *bp;
+  __shared__ int warp_cnt[kSchedThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int total = 0;
+  for (int base = 0; base < b.nslots; base += blockDim.x) {
+    const int s = base + threadIdx.x;
+    int st = SL_FREE;
+    if (s < b.nslots) st = b.state[s];
+    const bool in = st == SL_NEW || st == SL_CHECK;
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) warp_cnt[warp] = __popc(m);
+    __syncthreads();
+    int before = 0, sum = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) before += warp_cnt[w];
+      sum += warp_cnt[w];
+    }
+    if (in) b.lst[total + before + __popc(m & ((1u << lane) - 1u))] = s;
+    total += sum;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *b.lst_n = total;
+}
+
+// ---------------------------------------------------------------------------
+// zero x and d of newly assigned systems (CTA rows over the NEW / CHECK list)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) zero_kernel(const JuncDev* __restrict__ jt,
                                                            const BatchDev* __restrict__ bp) {
   using C = typename cx<T>::t;
   const BatchDev& b = *bp;
-  const int s = blockIdx.y;
-  if (b.state[s] != SL_NEW) return;
-  const JuncDev& J = jt[b.junc[s]];
-  if ((int)blockIdx.x >= J.nB) return;
-  const long long vo = b.voff[s], xo = b.xo[s];
-  const long long i0 = (long long)blockIdx.x * kVecPts, i1 = min(i0 + (long long)kVecPts, J.N);
-  C* dv = reinterpret_cast<C*>(b.d);
-  const bool keep_x = b.warm[s] != 0;
-  for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
-    if (!keep_x) b.x64[xo + i] = make_double2(0.0, 0.0);
-    dv[vo + i] = czero<C>();
+  const int n = *b.lst_n;
+  for (int li = blockIdx.y; li < n; li += gridDim.y) {
+    const int s = b.lst[li];
+    if (b.state[s] != SL_NEW) continue;
+    const JuncDev& J = jt[b.junc[s]];
+    if ((int)blockIdx.x >= J.nB) continue;
+    const long long vo = b.voff[s], xo = b.xo[s];
+    const long long i0 = (long long)blockIdx.x * kVecPts, i1 = min(i0 + (long long)kVecPts, J.N);
+    C* dv = reinterpret_cast<C*>(b.d);
+    const bool keep_x = b.warm[s] != 0;
+    for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
+      if (!keep_x) b.x64[xo + i] = make_double2(0.0, 0.0);
+      dv[vo + i] = czero<C>();
+    }
   }
 }
 
@@ -147,97 +179,106 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
   __shared__ double red[32 * 2];
   __shared__ int s_slot[SPB];
   __shared__ int s_any;
-  if (threadIdx.x == 0) s_any = 0;
-  __syncthreads();
-  if (threadIdx.x < SPB) {
-    const int s = blockIdx.y * SPB + threadIdx.x;
-    bool use = s < b.nslots;
-    if (use) {
-      if constexpr (MODE == PJ_R) {
-        use = b.state[s] == SL_ACTIVE;
-      } else if constexpr (MODE == PJ_X) {
-        const int st = b.state[s];
-        use = st == SL_NEW || st == SL_CHECK;
+  // PJ_X takes SPB entries of the NEW / CHECK list per CTA row (rows stride by
+  // gridDim.y); PJ_R and PJ_IN take slots blockIdx.y * SPB + u
+  int n_ent = b.nslots;
+  if constexpr (MODE == PJ_X) n_ent = *b.lst_n;
+  for (int base = blockIdx.y * SPB; base < n_ent; base += gridDim.y * SPB) {
+    __syncthreads();  // s_slot, s_any and red of the previous entries are consumed
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    if (threadIdx.x < SPB) {
+      const int e = base + threadIdx.x;
+      int s = e;
+      if constexpr (MODE == PJ_X) s = e < n_ent ? b.lst[e] : -1;
+      bool use = s >= 0 && s < b.nslots;
+      if (use) {
+        if constexpr (MODE == PJ_R) {
+          use = b.state[s] == SL_ACTIVE;
+        } else if constexpr (MODE == PJ_X) {
+          const int st = b.state[s];
+          use = st == SL_NEW || st == SL_CHECK;
+        }
       }
+      if (use && g >= jt[b.junc[s]].n_groups) use = false;
+      s_slot[threadIdx.x] = use ? s : -1;
+      if (use) atomicOr(&s_any, 1);
     }
-    if (use && g >= jt[b.junc[s]].n_groups) use = false;
-    s_slot[threadIdx.x] = use ? s : -1;
-    if (use) atomicOr(&s_any, 1);
-  }
-  __syncthreads();
-  if (!s_any) return;
-  int slot[SPB];
-  long long vo[SPB], xo[SPB];
-  double sig[SPB];
-#pragma unroll
-  for (int u = 0; u < SPB; ++u) {
-    slot[u] = s_slot[u];
-    const int s = slot[u] >= 0 ? slot[u] : 0;
-    vo[u] = b.voff[s];
-    xo[u] = (MODE == PJ_X) ? b.xo[s] : 0;
-    sig[u] = (MODE == PJ_X) ? b.sigma[s] : 1.0;
-  }
-  // every active slot of this CTA belongs to a junction with this group; the
-  // junction of the first active slot supplies the support (batches share it)
-  int s0 = 0;
-  for (int u = 0; u < SPB; ++u)
-    if (slot[u] >= 0) {
-      s0 = slot[u];
-      break;
-    }
-  const JuncDev& J = jt[b.junc[s0]];
-  const int p0 = J.grp_p0[g], np = J.grp_np[g];
-  const int k0 = J.grp_ptr[g], k1 = J.grp_ptr[g + 1], len = k1 - k0;
-  const long long vb = J.grp_voff[g];
-  C acc[SPB][NP];
-#pragma unroll
-  for (int u = 0; u < SPB; ++u)
-#pragma unroll
-    for (int p = 0; p < NP; ++p) acc[u][p] = czero<C>();
-  for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
-    const int gi = J.grp_idx[kk];
-    const long long vk = vb + (kk - k0);
-    CT a[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      if (p < np) {
-        if constexpr (sizeof(CT) == 8) a[p] = (CT)J.grp_val64[vk + (long long)p * len];
-        else a[p] = (CT)J.grp_val32[vk + (long long)p * len];
-      } else {
-        a[p] = 0;
-      }
-    }
-#pragma unroll
+    __syncthreads();
+    if (!s_any) continue;
+    int slot[SPB];
+    long long vo[SPB], xo[SPB];
+    double sig[SPB];
+  #pragma unroll
     for (int u = 0; u < SPB; ++u) {
-      if (slot[u] < 0) continue;
-      C v;
-      if constexpr (MODE == PJ_R) {
-        v = reinterpret_cast<const CO*>(b.r)[vo[u] + gi];
-      } else if constexpr (MODE == PJ_X) {
-        const double2 xx = b.x64[xo[u] + gi];
-        const double2 dd = to64(reinterpret_cast<const CO*>(b.d)[vo[u] + gi]);
-        v = mk2(fma(sig[u], dd.x, xx.x), fma(sig[u], dd.y, xx.y));
-      } else {
-        v = reinterpret_cast<const CO*>(x_in)[vo[u] + gi];
-      }
-#pragma unroll
-      for (int p = 0; p < NP; ++p) acc[u][p] = rfma(a[p], v, acc[u][p]);
+      slot[u] = s_slot[u];
+      const int s = slot[u] >= 0 ? slot[u] : 0;
+      vo[u] = b.voff[s];
+      xo[u] = (MODE == PJ_X) ? b.xo[s] : 0;
+      sig[u] = (MODE == PJ_X) ? b.sigma[s] : 1.0;
     }
-  }
-#pragma unroll
-  for (int u = 0; u < SPB; ++u) {
-    if (slot[u] < 0) continue;  // uniform across the CTA
-    C* out = reinterpret_cast<C*>(c_out) + (size_t)slot[u] * J.n_proj + p0;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      if (p < np) {  // uniform across the CTA
-        CT v[2] = {acc[u][p].x, acc[u][p].y};
-        double o[2];
-        block_sum<2>(v, red, o);
-        if (threadIdx.x == 0) out[p] = mk2((CT)o[0], (CT)o[1]);
+    // every active slot of this CTA belongs to a junction with this group; the
+    // junction of the first active slot supplies the support (batches share it)
+    int s0 = 0;
+    for (int u = 0; u < SPB; ++u)
+      if (slot[u] >= 0) {
+        s0 = slot[u];
+        break;
+      }
+    const JuncDev& J = jt[b.junc[s0]];
+    const int p0 = J.grp_p0[g], np = J.grp_np[g];
+    const int k0 = J.grp_ptr[g], k1 = J.grp_ptr[g + 1], len = k1 - k0;
+    const long long vb = J.grp_voff[g];
+    C acc[SPB][NP];
+  #pragma unroll
+    for (int u = 0; u < SPB; ++u)
+  #pragma unroll
+      for (int p = 0; p < NP; ++p) acc[u][p] = czero<C>();
+    for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
+      const int gi = J.grp_idx[kk];
+      const long long vk = vb + (kk - k0);
+      CT a[NP];
+  #pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (p < np) {
+          if constexpr (sizeof(CT) == 8) a[p] = (CT)J.grp_val64[vk + (long long)p * len];
+          else a[p] = (CT)J.grp_val32[vk + (long long)p * len];
+        } else {
+          a[p] = 0;
+        }
+      }
+  #pragma unroll
+      for (int u = 0; u < SPB; ++u) {
+        if (slot[u] < 0) continue;
+        C v;
+        if constexpr (MODE == PJ_R) {
+          v = reinterpret_cast<const CO*>(b.r)[vo[u] + gi];
+        } else if constexpr (MODE == PJ_X) {
+          const double2 xx = b.x64[xo[u] + gi];
+          const double2 dd = to64(reinterpret_cast<const CO*>(b.d)[vo[u] + gi]);
+          v = mk2(fma(sig[u], dd.x, xx.x), fma(sig[u], dd.y, xx.y));
+        } else {
+          v = reinterpret_cast<const CO*>(x_in)[vo[u] + gi];
+        }
+  #pragma unroll
+        for (int p = 0; p < NP; ++p) acc[u][p] = rfma(a[p], v, acc[u][p]);
       }
     }
-  }
+  #pragma unroll
+    for (int u = 0; u < SPB; ++u) {
+      if (slot[u] < 0) continue;  // uniform across the CTA
+      C* out = reinterpret_cast<C*>(c_out) + (size_t)slot[u] * J.n_proj + p0;
+  #pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (p < np) {  // uniform across the CTA
+          CT v[2] = {acc[u][p].x, acc[u][p].y};
+          double o[2];
+          block_sum<2>(v, red, o);
+          if (threadIdx.x == 0) out[p] = mk2((CT)o[0], (CT)o[1]);
+        }
+      }
+    }
+  }  // list entries
 }
 
 // ---------------------------------------------------------------------------
@@ -299,7 +340,6 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
   const BatchDev& b = *bp;
   const int S = b.nslots;
   __shared__ int warp_cnt[32];
-  __shared__ int s_next;
   __shared__ double red[32 * 2];
   int upd = 0, busy = 0;
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
@@ -393,39 +433,58 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
     b.state[s] = st;
   }
   __syncthreads();
-  // assign queued systems to FREE slots, in slot order and queue (FIFO) order;
-  // a system whose dependency has not finished blocks the queue.
-  __shared__ int first_bad, stop;
-  if (threadIdx.x == 0) {
-    s_next = b.sched[0];
-    stop = 0;
-  }
-  __syncthreads();
+  // Assign ready systems to FREE slots.  Free slots are taken in slot order,
+  // systems in queue order from the first unstarted one, skipping those whose
+  // dependency has not finished: an adjoint waits for its forward column but
+  // does not hold up the systems queued behind it.  At most kReadyWindow
+  // systems past the first unstarted one are examined.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  __shared__ int s_nf, s_done, s_first;
+  // (1) the free slots, compacted in slot order
+  if (threadIdx.x == 0) s_nf = 0;
+  __syncthreads();
   for (int base = 0; base < S; base += blockDim.x) {
-    if (stop) break;  // uniform: read after a barrier
     const int s = base + threadIdx.x;
     const bool fr = s < S && b.state[s] == SL_FREE;
     const unsigned m = __ballot_sync(0xffffffffu, fr);
     if (lane == 0) warp_cnt[warp] = __popc(m);
-    if (threadIdx.x == 0) first_bad = 0x7fffffff;
     __syncthreads();
     int before = 0, total = 0;
     for (int w = 0; w < nw; ++w) {
       if (w < warp) before += warp_cnt[w];
       total += warp_cnt[w];
     }
-    const int rank = before + __popc(m & ((1u << lane) - 1u));
-    const int next = s_next;
-    const int n = next + rank;
+    if (fr) b.fslot[s_nf + before + __popc(m & below)] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) s_nf += total;
+    __syncthreads();
+  }
+  const int nf = s_nf;
+  const int next0 = b.sched[0];
+  // (2) ready systems, in queue order, to the free slots
+  if (threadIdx.x == 0) s_done = 0;
+  __syncthreads();
+  const int wend = min(b.nsys, next0 + kReadyWindow);
+  for (int base = next0; base < wend && nf > 0; base += blockDim.x) {
+    if (s_done >= nf) break;  // uniform: written before the last barrier
+    const int n = base + threadIdx.x;
     bool ready = false;
-    if (fr && n < b.nsys) {
+    if (n < wend && !b.sys_started[n]) {
       const int dep = b.sys_dep ? b.sys_dep[n] : -1;
       ready = dep < 0 || b.out_status[dep] >= 0;
     }
-    if (fr && !ready) atomicMin(&first_bad, rank);
+    const unsigned m = __ballot_sync(0xffffffffu, ready);
+    if (lane == 0) warp_cnt[warp] = __popc(m);
     __syncthreads();
-    if (fr && rank < first_bad) {
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) before += warp_cnt[w];
+      total += warp_cnt[w];
+    }
+    const int k = s_done + before + __popc(m & below);
+    if (ready && k < nf) {
+      const int s = b.fslot[k];
       b.sys[s] = n;
       b.junc[s] = b.sys_junc[n];
       b.E[s] = b.sys_E[n];
@@ -435,21 +494,29 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
       b.xfo[s] = b.sys_xfo[n];
       b.warm[s] = (b.sys_bn2 != nullptr && b.sys_bn2[n] > 0.0) ? 1 : 0;
       b.state[s] = SL_NEW;
+      b.sys_started[n] = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const int assigned = total < first_bad ? total : first_bad;
-      s_next = next + assigned;
-      if (first_bad != 0x7fffffff) stop = 1;
-    }
+    if (threadIdx.x == 0) s_done = min(nf, s_done + total);
     __syncthreads();
+  }
+  // (3) the first unstarted system
+  if (threadIdx.x == 0) s_first = b.nsys;
+  __syncthreads();
+  for (int base = next0; base < b.nsys; base += blockDim.x) {
+    const int n = base + threadIdx.x;
+    if (n < b.nsys && !b.sys_started[n]) atomicMin(&s_first, n);
+    __syncthreads();
+    const bool found = s_first < b.nsys;
+    __syncthreads();
+    if (found) break;
   }
   for (int s = threadIdx.x; s < S; s += blockDim.x) busy += (b.state[s] != SL_FREE) ? 1 : 0;
   double v[2] = {(double)busy, (double)upd};
   double out[2];
   block_sum<2>(v, red, out);
   if (threadIdx.x == 0) {
-    b.sched[0] = s_next;
+    b.sched[0] = s_first;
     b.sched[1] = (int)out[0];
     b.sched[3 + slot_it] = (int)out[0];
     b.sched[3 + kMaxGraphIters + slot_it] = 0;  // counted by the bookkeeping kernel of this iteration
@@ -468,48 +535,52 @@ __global__ void __launch_bounds__(kVecThreads) x_update_kernel(const JuncDev* __
                                                                const BatchDev* __restrict__ bp) {
   using C = typename cx<T>::t;
   const BatchDev& b = *bp;
-  const int s = blockIdx.y;
-  const int st = b.state[s];
-  if (st != SL_NEW && st != SL_CHECK) return;
-  const JuncDev& J = jt[b.junc[s]];
-  if ((int)blockIdx.x >= J.nB) return;
   __shared__ double s_part[kVecThreads];
   __shared__ double s_sig;
-  if (st == SL_NEW) {
-    // ||b||^2 from the residual kernel's partials, in the fixed order of the
-    // update kernel's mu sum
-    double n2t = 0.0;
-    for (int t = threadIdx.x; t < J.nR; t += kVecThreads) n2t += b.nrm0_part[(size_t)s * b.PA + t];
-    s_part[threadIdx.x] = n2t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double n2 = 0.0;
-      for (int t = 0; t < kVecThreads && t < J.nR; ++t) n2 += s_part[t];
-      s_sig = n2 > 0.0 ? sqrt(n2) : 1.0;
-      if (blockIdx.x == 0) b.sigma[s] = s_sig;
+  const int n = *b.lst_n;
+  for (int li = blockIdx.y; li < n; li += gridDim.y) {
+    const int s = b.lst[li];
+    const int st = b.state[s];
+    if (st != SL_NEW && st != SL_CHECK) continue;
+    const JuncDev& J = jt[b.junc[s]];
+    if ((int)blockIdx.x >= J.nB) continue;
+    __syncthreads();  // s_part / s_sig of the previous entry are consumed
+    if (st == SL_NEW) {
+      // ||b||^2 from the residual kernel's partials, in the fixed order of the
+      // update kernel's mu sum
+      double n2t = 0.0;
+      for (int t = threadIdx.x; t < J.nR; t += kVecThreads) n2t += b.nrm0_part[(size_t)s * b.PA + t];
+      s_part[threadIdx.x] = n2t;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double n2 = 0.0;
+        for (int t = 0; t < kVecThreads && t < J.nR; ++t) n2 += s_part[t];
+        s_sig = n2 > 0.0 ? sqrt(n2) : 1.0;
+        if (blockIdx.x == 0) b.sigma[s] = s_sig;
+      }
+    } else if (threadIdx.x == 0) {
+      s_sig = b.sigma[s];
     }
-  } else if (threadIdx.x == 0) {
-    s_sig = b.sigma[s];
-  }
-  __syncthreads();
-  const double sig = s_sig;
-  const T isig = (T)(1.0 / sig);
-  const long long vo = b.voff[s], xo = b.xo[s];
-  const long long i0 = (long long)blockIdx.x * kVecPts;
-  const long long i1 = min(i0 + (long long)kVecPts, J.N);
-  C* dv = reinterpret_cast<C*>(b.d);
-  C* rv = reinterpret_cast<C*>(b.r);
-  for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
-    const double2 d = to64(dv[vo + i]);
-    double2 x = b.x64[xo + i];
-    x.x = fma(sig, d.x, x.x);
-    x.y = fma(sig, d.y, x.y);
-    b.x64[xo + i] = x;
-    dv[vo + i] = czero<C>();
-    C r = rv[vo + i];
-    r.x *= isig;
-    r.y *= isig;
-    rv[vo + i] = r;
+    __syncthreads();
+    const double sig = s_sig;
+    const T isig = (T)(1.0 / sig);
+    const long long vo = b.voff[s], xo = b.xo[s];
+    const long long i0 = (long long)blockIdx.x * kVecPts;
+    const long long i1 = min(i0 + (long long)kVecPts, J.N);
+    C* dv = reinterpret_cast<C*>(b.d);
+    C* rv = reinterpret_cast<C*>(b.r);
+    for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
+      const double2 d = to64(dv[vo + i]);
+      double2 x = b.x64[xo + i];
+      x.x = fma(sig, d.x, x.x);
+      x.y = fma(sig, d.y, x.y);
+      b.x64[xo + i] = x;
+      dv[vo + i] = czero<C>();
+      C r = rv[vo + i];
+      r.x *= isig;
+      r.y *= isig;
+      rv[vo + i] = r;
+    }
   }
 }
 
@@ -677,6 +748,11 @@ cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, cons
   dim3 grid(nB, nslots);
   if (fp32) x_update_kernel<float><<<grid, kVecThreads, 0, st>>>(jt, b);
   else x_update_kernel<double><<<grid, kVecThreads, 0, st>>>(jt, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list(cudaStream_t st, const BatchDev* b) {
+  list_kernel<<<1, kSchedThreads, 0, st>>>(b);
   return cudaGetLastError();
 }
 
