@@ -14,13 +14,16 @@
 // The value fed to the stencil is produced on the fly, which fuses the
 // neighbouring vector update into the matvec:
 //   OP_COCG : v = r + beta p_old   (COCG direction update), writes p_new = v,
-//             q = A v and the partial sums of mu = v^T q (unconjugated).
+//             q = A_loc v (A without the projector term) and the partial sums
+//             of mu = v^T A v (unconjugated); the projector term of A v is
+//             added to q by the update kernel, its share of mu comes from the
+//             projections (-sum_p e_kb[p] c_p^2).
 //   OP_RESID: v = x64 + d          (refinement iterate), writes r = b - A v,
 //             and partial sums of ||r||^2 and r^T r; computed in FP64.
 //   OP_APPLY: v = x (input),  y = A v.
 // The projector term uses ce[p] = e_kb[p] (v_p . v), prepared per CTA from the
-// projections computed by the gather kernel; each grid point adds
-// -sum over its (p, value) entries.
+// projections computed by the gather kernel; each grid point adds -sum over
+// its atom entries of the projector values times ce.
 #pragma once
 #include <type_traits>
 
@@ -55,6 +58,26 @@ __device__ __forceinline__ void kahan_add(S& sum, S& carry, S term) {
   const S t = sum + y;
   carry = (t - sum) - y;
   sum = t;
+}
+
+// y -= sum_j a_j cp[j] over one quad of an atom entry's projector values
+// (FP64 values for an FP64 compute type, else FP32), in projector order.
+template <typename C, typename CT>
+__device__ __forceinline__ C proj_quad(const JuncDev& J, int qi, const C* cp, C y) {
+  if constexpr (sizeof(CT) == 8) {
+    const double2 a01 = J.inv_q64[2 * (size_t)qi], a23 = J.inv_q64[2 * (size_t)qi + 1];
+    y = rfma((CT)-a01.x, cp[0], y);
+    y = rfma((CT)-a01.y, cp[1], y);
+    y = rfma((CT)-a23.x, cp[2], y);
+    y = rfma((CT)-a23.y, cp[3], y);
+  } else {
+    const float4 a = J.inv_q32[qi];
+    y = rfma((CT)-a.x, cp[0], y);
+    y = rfma((CT)-a.y, cp[1], y);
+    y = rfma((CT)-a.z, cp[2], y);
+    y = rfma((CT)-a.w, cp[3], y);
+  }
+  return y;
 }
 
 template <typename T, int MODE> struct RawIn;
@@ -122,20 +145,13 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
   }
 
   // ---- projector coefficients ce[p] = e_kb[p] * (v_p . v) -------------------
+  // (COCG: none.  The projector term of q = A p is added by the update
+  // kernel, and the projection kernel forms c_p = v_p . p of the new direction,
+  // e_kb c_p and the term's share of mu, -sum_p e_kb[p] c_p^2 (p^T v_p = c_p,
+  // unconjugated), from the projections alone.)
   const int n_proj = J.n_proj;
-  if (n_proj > 0) {
-    if constexpr (MODE == OP_COCG) {
-      const CO* cr = reinterpret_cast<const CO*>(b.c_r) + (size_t)s * n_proj;
-      const CO* cpo = reinterpret_cast<const CO*>(b.c_p) + ((size_t)(k & 1) * b.nslots + s) * n_proj;
-      CO* cpn = reinterpret_cast<CO*>(b.c_p) + ((size_t)((k + 1) & 1) * b.nslots + s) * n_proj;
-      for (int p = tid; p < n_proj; p += nt) {
-        C c = cr[p];
-        if (!first) c = cfma(beta, (C)cpo[p], c);
-        if (tile == 0) cpn[p] = c;
-        const CT e = (CT)J.ekb[p];
-        ce[p] = mk2(e * c.x, e * c.y);
-      }
-    } else if constexpr (MODE == OP_RESID) {
+  if (MODE != OP_COCG && n_proj > 0) {
+    if constexpr (MODE == OP_RESID) {
       const double2* cxp = b.c_x + (size_t)s * n_proj;
       for (int p = tid; p < n_proj; p += nt) {
         const double e = J.ekb[p];
@@ -149,6 +165,7 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
         ce[p] = mk2(e * c.x, e * c.y);
       }
     }
+    for (int p = tid; p < kCePad; p += nt) ce[n_proj + p] = czero<C>();
   }
 
   // ---- owned points and halo rows -----------------------------------------
@@ -235,7 +252,7 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
       if (own[u] && z < z1) {
         const long long g = (long long)z * plane + po[u];
         if constexpr (sizeof(CT) == 4) dgf_n[u] = J.dg32[g];
-        if (n_proj > 0) {
+        if (MODE != OP_COCG && n_proj > 0) {
           e0_n[u] = J.inv_ptr[g];
           e1_n[u] = J.inv_ptr[g + 1];
         }
@@ -300,13 +317,11 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
       } else {
         y = fd_diff_form<C, CT, R>(qv[u], smb, so[u], pitch, wst, vc, dgf_c[u], E);
       }
-      if (n_proj > 0) {
-        const int e0 = e0_c[u], e1 = e1_c[u];
+      if (MODE != OP_COCG && n_proj > 0) {
+        const int e0 = e0_c[u], e1 = e1_c[u], nq = J.inv_nq;
         for (int e = e0; e < e1; ++e) {
-          CT a;
-          if constexpr (sizeof(CT) == 8) a = (CT)J.inv_val64[e];
-          else a = (CT)J.inv_val32[e];
-          y = rfma(-a, ce[J.inv_proj[e]], y);
+          const C* cp = ce + J.inv_p0[e];
+          for (int qd = 0; qd < nq; ++qd) y = proj_quad<C, CT>(J, e * nq + qd, cp + 4 * qd, y);
         }
       }
       if constexpr (MODE == OP_COCG) {
@@ -446,7 +461,7 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
   C* ce = exch + 2 * prow * pitch;                   // [n_proj]
   const int n_proj = J.n_proj;
   uint64_t* bars = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(ce + n_proj) + 15) & ~static_cast<uintptr_t>(15));
+      (reinterpret_cast<uintptr_t>(ce + n_proj + kCePad) + 15) & ~static_cast<uintptr_t>(15));
   __shared__ double red[32 * 2];
   __shared__ int s_bad;
 
@@ -470,19 +485,9 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
   } else {
     src0 = reinterpret_cast<const C*>(x_in) + vo;
   }
-  if (n_proj > 0) {
-    if constexpr (MODE == OP_COCG) {
-      const C* cr = reinterpret_cast<const C*>(b.c_r) + (size_t)s * n_proj;
-      const C* cpo = reinterpret_cast<const C*>(b.c_p) + ((size_t)(k & 1) * b.nslots + s) * n_proj;
-      C* cpn = reinterpret_cast<C*>(b.c_p) + ((size_t)((k + 1) & 1) * b.nslots + s) * n_proj;
-      for (int p = tid; p < n_proj; p += nt) {
-        C c = cr[p];
-        if (!first) c = cfma(beta, cpo[p], c);
-        if (tile == 0) cpn[p] = c;
-        const T e = (T)J.ekb[p];
-        ce[p] = mk2(e * c.x, e * c.y);
-      }
-    } else {
+  // COCG: no coefficients, the projector term of q is added by the update kernel
+  if (MODE != OP_COCG && n_proj > 0) {
+    {
       const C* cin = reinterpret_cast<const C*>(c_in) + (size_t)s * n_proj;
       for (int p = tid; p < n_proj; p += nt) {
         const T e = (T)J.ekb[p];
@@ -490,6 +495,7 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
         ce[p] = mk2(e * c.x, e * c.y);
       }
     }
+    for (int p = tid; p < kCePad; p += nt) ce[n_proj + p] = czero<C>();
   }
   __syncthreads();
 
@@ -530,7 +536,7 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
     if (own && z < z1) {
       const long long g = (long long)z * plane + tid;
       if constexpr (sizeof(T) == 4) dg_n = J.dg32[g];
-      if (n_proj > 0) {
+      if (MODE != OP_COCG && n_proj > 0) {
         e0_n = J.inv_ptr[g];
         e1_n = J.inv_ptr[g + 1];
       }
@@ -591,12 +597,11 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
     } else {
       y = fd_diff_form<C, T, R>(qv, smb, so, pitch, wst, vc, dg_c, E);
     }
-    if (n_proj > 0) {
+    if (MODE != OP_COCG && n_proj > 0) {
+      const int nq = J.inv_nq;
       for (int e = e0; e < e1; ++e) {
-        T a;
-        if constexpr (sizeof(T) == 8) a = (T)J.inv_val64[e];
-        else a = (T)J.inv_val32[e];
-        y = rfma(-a, ce[J.inv_proj[e]], y);
+        const C* cp = ce + J.inv_p0[e];
+        for (int qd = 0; qd < nq; ++qd) y = proj_quad<C, T>(J, e * nq + qd, cp + 4 * qd, y);
       }
     }
     if constexpr (MODE == OP_COCG) {

@@ -71,7 +71,7 @@ struct Workspace {
   DevBuf Xslot, r, p0, p1, q, d;
   DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, stall, warm, rho_cur, beta_cur;
   DevBuf bnorm2, sigma, rlast2, rrec2, tol2;
-  DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters, lst, lst_n, fslot;
+  DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters, lst, lst_n, fslot, c_e;
   int generation = 0;
 };
 
@@ -111,7 +111,7 @@ struct rsn_ctx {
   bool dirty = true;
 
   // device operator data
-  DevBuf dg64, dg32, gld, L_idx, L_gam, inv_ptr, inv_proj, inv_val64, inv_val32;
+  DevBuf dg64, dg32, gld, L_idx, L_gam, inv_ptr, inv_p0, inv_q64, inv_q32;
   DevBuf grp_ptr, grp_p0, grp_np, grp_voff, grp_idx, grp_val64, grp_val32, ekb;
   int n_groups = 0, nL = 0, max_np = 1;
   JuncDev jh{};
@@ -297,24 +297,31 @@ static rsn_status commit_setup(rsn_ctx* c) {
       gptr.push_back((int)gidx.size());
       p = q;
     }
-    for (int k = 0; k < np; ++k)
-      for (int64_t e = c->poff[k]; e < c->poff[k + 1]; ++e) cnt[c->pidx[e] + 1]++;
   }
   c->n_groups = (int)gp0.size();
   c->max_np = 1;
   for (int v : gnp) c->max_np = std::max(c->max_np, v);
+  // per grid point, one entry per atom whose support holds it: the atom's
+  // first projector and its projector values there, padded with zeros to
+  // quads (4 values) so that the operator kernel reads them as vectors
+  const int nq = (c->max_np + 3) / 4;
+  const int G = c->n_groups;
+  for (int g = 0; g < G; ++g)
+    for (int k = gptr[g]; k < gptr[g + 1]; ++k) cnt[gidx[k] + 1]++;
   for (long long i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
-  const size_t nnz = (size_t)cnt[N];
-  std::vector<int> iproj(std::max<size_t>(1, nnz)), fill(cnt.begin(), cnt.end() - 1);
-  std::vector<double> ival(std::max<size_t>(1, nnz));
-  for (int k = 0; k < np; ++k)
-    for (int64_t e = c->poff[k]; e < c->poff[k + 1]; ++e) {
-      const int i = c->pidx[e];
-      iproj[fill[i]] = k;
-      ival[fill[i]] = c->pval[e];
-      fill[i]++;
+  const size_t nent = (size_t)cnt[N];
+  std::vector<int> ip0(std::max<size_t>(1, nent)), fill(cnt.begin(), cnt.end() - 1);
+  std::vector<double> iq64(std::max<size_t>(1, nent) * 4 * nq, 0.0);
+  for (int g = 0; g < G; ++g) {
+    const int len = gptr[g + 1] - gptr[g];
+    for (int k = 0; k < len; ++k) {
+      const int i = gidx[gptr[g] + k];
+      const int e = fill[i]++;
+      ip0[e] = gp0[g];
+      for (int j = 0; j < gnp[g]; ++j) iq64[(size_t)e * 4 * nq + j] = gval[gvoff[g] + (size_t)j * len + k];
     }
-  std::vector<float> ivalf(ival.begin(), ival.end()), gvalf(gval.begin(), gval.end());
+  }
+  std::vector<float> iq32(iq64.begin(), iq64.end()), gvalf(gval.begin(), gval.end());
   auto up = [&](DevBuf& b, const void* src, size_t bytes) -> cudaError_t {
     cudaError_t e = b.ensure(std::max<size_t>(bytes, 16));
     if (e != cudaSuccess) return e;
@@ -322,9 +329,9 @@ static rsn_status commit_setup(rsn_ctx* c) {
     return cudaSuccess;
   };
   RSN_CUDA(c, up(c->inv_ptr, cnt.data(), (N + 1) * sizeof(int)));
-  RSN_CUDA(c, up(c->inv_proj, iproj.data(), nnz * sizeof(int)));
-  RSN_CUDA(c, up(c->inv_val64, ival.data(), nnz * sizeof(double)));
-  RSN_CUDA(c, up(c->inv_val32, ivalf.data(), nnz * sizeof(float)));
+  RSN_CUDA(c, up(c->inv_p0, ip0.data(), nent * sizeof(int)));
+  RSN_CUDA(c, up(c->inv_q64, iq64.data(), nent * 4 * nq * sizeof(double)));
+  RSN_CUDA(c, up(c->inv_q32, iq32.data(), nent * 4 * nq * sizeof(float)));
   RSN_CUDA(c, up(c->grp_ptr, gptr.data(), gptr.size() * sizeof(int)));
   RSN_CUDA(c, up(c->grp_p0, gp0.data(), gp0.size() * sizeof(int)));
   RSN_CUDA(c, up(c->grp_np, gnp.data(), gnp.size() * sizeof(int)));
@@ -355,9 +362,10 @@ static rsn_status commit_setup(rsn_ctx* c) {
   J.n_proj = np;
   J.n_groups = c->n_groups;
   J.inv_ptr = c->inv_ptr.as<int>();
-  J.inv_proj = c->inv_proj.as<int>();
-  J.inv_val64 = c->inv_val64.as<double>();
-  J.inv_val32 = c->inv_val32.as<float>();
+  J.inv_nq = (c->max_np + 3) / 4;
+  J.inv_p0 = c->inv_p0.as<int>();
+  J.inv_q64 = c->inv_q64.as<double2>();
+  J.inv_q32 = c->inv_q32.as<float4>();
   J.grp_ptr = c->grp_ptr.as<int>();
   J.grp_p0 = c->grp_p0.as<int>();
   J.grp_np = c->grp_np.as<int>();
@@ -629,7 +637,8 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   Workspace& w = c->ws;
   const long long N = c->N;
   const Tiling ti = choose_tiling(c, !fp32, OP_COCG, S), tr = choose_tiling(c, true, OP_RESID, S);
-  const int PA = std::max(ti.n, tr.n), PB = c->jh.nB;
+  // mu partials: the operator tiles', then one per atom (projection kernel)
+  const int PA = std::max(ti.n + c->n_groups, tr.n), PB = c->jh.nB;
   if (w.slots == S && w.fp32 == fp32 && w.N == N && w.PA == PA && w.PB == PB && w.n_proj == c->n_proj)
     return RSN_OK;
   const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
@@ -672,6 +681,8 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   RSN_CUDA(c, w.c_r.ensure((size_t)S * npj * sizeof(double2)));
   RSN_CUDA(c, w.c_p.ensure(2 * (size_t)S * npj * sizeof(double2)));
   RSN_CUDA(c, w.c_x.ensure((size_t)S * npj * sizeof(double2)));
+  RSN_CUDA(c, w.c_e.ensure((size_t)S * (npj + kCePad) * sizeof(double2)));
+  RSN_CUDA(c, cudaMemset(w.c_e.p, 0, (size_t)S * (npj + kCePad) * sizeof(double2)));
   RSN_CUDA(c, w.sched.ensure((3 + 2 * kMaxGraphIters) * sizeof(int)));
   RSN_CUDA(c, w.counters.ensure(4 * sizeof(unsigned long long)));
   RSN_CUDA(c, w.lst.ensure(si));
@@ -792,6 +803,8 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.lst = w.lst.as<int>();
   b.lst_n = w.lst_n.as<int>();
   b.fslot = w.fslot.as<int>();
+  b.c_e = w.c_e.p;
+  b.ce_stride = std::max(1, c->n_proj) + kCePad;
   b.tol = o->tol;
   b.tol_adj = o->tol_adjoint > 0 ? o->tol_adjoint : o->tol;
   b.delta = o->tol_inner;

@@ -19,6 +19,9 @@ namespace rsn {
 constexpr int kMaxR = 6;        // up to the order-12 stencil
 constexpr int kMaxPlane = 4096; // nx*ny limit (smem plane tiles)
 constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
+// zero entries after the n_proj projector coefficients in shared memory, read
+// by the zero-padded tail of an atom's last value quad
+constexpr int kCePad = 16;
 constexpr int kMaxGraphIters = 256;
 constexpr int kSchedThreads = 1024;
 // CTA rows of the kernels that work only on NEW / CHECK slots (zero, true
@@ -49,10 +52,14 @@ struct JuncDev {
   const double* L_gam;
   // projectors
   int n_proj, n_groups;
+  // per grid point i, entries inv_ptr[i] .. inv_ptr[i+1]-1, one per atom whose
+  // support holds i: the atom's first projector inv_p0[e] and the values of
+  // its projectors at i in inv_nq quads (zero-padded), FP64 as 2 double2 per quad
   const int* inv_ptr;
-  const int* inv_proj;
-  const double* inv_val64;
-  const float* inv_val32;
+  int inv_nq;
+  const int* inv_p0;
+  const double2* inv_q64;
+  const float4* inv_q32;
   const int* grp_ptr;
   const int* grp_p0;
   const int* grp_np;
@@ -138,6 +145,8 @@ struct BatchDev {
   int* lst;                  // NEW / CHECK slots of the current iteration, in slot order
   int* lst_n;                // their number
   int* fslot;                // FREE slots in slot order (scheduler scratch)
+  void* c_e;                 // e_kb[p] c_p[p] of the current direction per slot (inner precision),
+  int ce_stride;             // n_proj + kCePad entries per slot, the last kCePad always zero
   // options
   double tol, delta;
   double tol_adj;  // tolerance of systems with a computed right-hand side (col < 0)

@@ -95,10 +95,11 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
   __shared__ double2 s_mu[kVecThreads];
   __shared__ double2 s_alpha;
   const int k = b.iters[s];
-  // mu = p^T A p from the operator kernel's partials (any number of tiles):
-  // thread t adds partials t, t + 256, ... and thread 0 adds those sums in
-  // thread order, so the order is fixed for a given tiling
-  const int nA = J.nA;
+  // mu = p^T A p from the operator kernel's partials (any number of tiles)
+  // followed by one partial per atom from the projection kernel: thread t adds
+  // partials t, t + 256, ... and thread 0 adds those sums in thread order, so
+  // the order is fixed for a given tiling
+  const int nA = J.nA + (J.n_proj > 0 ? J.n_groups : 0);
   {
     double2 m = make_double2(0.0, 0.0);
     for (int t = threadIdx.x; t < nA; t += kVecThreads) {
@@ -132,11 +133,23 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
   C* dv = reinterpret_cast<C*>(b.d);
   const long long i0 = (long long)blockIdx.x * kVecPts;
   const long long i1 = min(i0 + (long long)kVecPts, J.N);
+  // the operator kernel leaves out the projector term of q = A p: it is added
+  // here, q(i) -= sum over the atom entries of i of v_p(i) e_kb[p] c_p, with
+  // e_kb c_p of the new direction from the operator kernel (zero-padded)
+  const int n_proj = J.n_proj, nq = J.inv_nq;
+  const C* cen = reinterpret_cast<const C*>(b.c_e) + (size_t)s * b.ce_stride;
   T nrm = 0, rre = 0, rim = 0;
   for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
     const long long g = vo + i;
     const C p = pn[g];
-    const C q = qv[g];
+    C q = qv[g];
+    if (n_proj > 0) {
+      const int e0 = J.inv_ptr[i], e1 = J.inv_ptr[i + 1];
+      for (int e = e0; e < e1; ++e) {
+        const C* cp = cen + J.inv_p0[e];
+        for (int qd = 0; qd < nq; ++qd) q = proj_quad<C, T>(J, e * nq + qd, cp + 4 * qd, q);
+      }
+    }
     C r = rv[g];
     r.x -= alpha.x * q.x - alpha.y * q.y;
     r.y -= alpha.x * q.y + alpha.y * q.x;
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
     int slot[SPB];
     long long vo[SPB], xo[SPB];
     double sig[SPB];
-  #pragma unroll
+#pragma unroll
     for (int u = 0; u < SPB; ++u) {
       slot[u] = s_slot[u];
       const int s = slot[u] >= 0 ? slot[u] : 0;
@@ -230,15 +243,15 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
     const int k0 = J.grp_ptr[g], k1 = J.grp_ptr[g + 1], len = k1 - k0;
     const long long vb = J.grp_voff[g];
     C acc[SPB][NP];
-  #pragma unroll
+#pragma unroll
     for (int u = 0; u < SPB; ++u)
-  #pragma unroll
+#pragma unroll
       for (int p = 0; p < NP; ++p) acc[u][p] = czero<C>();
     for (int kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
       const int gi = J.grp_idx[kk];
       const long long vk = vb + (kk - k0);
       CT a[NP];
-  #pragma unroll
+#pragma unroll
       for (int p = 0; p < NP; ++p) {
         if (p < np) {
           if constexpr (sizeof(CT) == 8) a[p] = (CT)J.grp_val64[vk + (long long)p * len];
@@ -247,7 +260,7 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
           a[p] = 0;
         }
       }
-  #pragma unroll
+#pragma unroll
       for (int u = 0; u < SPB; ++u) {
         if (slot[u] < 0) continue;
         C v;
@@ -260,23 +273,47 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
         } else {
           v = reinterpret_cast<const CO*>(x_in)[vo[u] + gi];
         }
-  #pragma unroll
+#pragma unroll
         for (int p = 0; p < NP; ++p) acc[u][p] = rfma(a[p], v, acc[u][p]);
       }
     }
-  #pragma unroll
+#pragma unroll
     for (int u = 0; u < SPB; ++u) {
       if (slot[u] < 0) continue;  // uniform across the CTA
-      C* out = reinterpret_cast<C*>(c_out) + (size_t)slot[u] * J.n_proj + p0;
-  #pragma unroll
+      const int sl = slot[u];
+      C* out = reinterpret_cast<C*>(c_out) + (size_t)sl * J.n_proj + p0;
+      // PJ_R, thread 0: the projections of the new direction
+      // c_p = c_r + beta c_p_old (c_p = c_r in the first iteration), e_kb c_p
+      // for the update kernel, and this atom's share of mu = p^T A p,
+      // -sum_p e_kb[p] c_p^2, as one more partial after the operator tiles'
+      double2 mu_g = make_double2(0.0, 0.0);
+#pragma unroll
       for (int p = 0; p < NP; ++p) {
         if (p < np) {  // uniform across the CTA
           CT v[2] = {acc[u][p].x, acc[u][p].y};
           double o[2];
           block_sum<2>(v, red, o);
-          if (threadIdx.x == 0) out[p] = mk2((CT)o[0], (CT)o[1]);
+          if (threadIdx.x == 0) {
+            const C cr = mk2((CT)o[0], (CT)o[1]);
+            out[p] = cr;
+            if constexpr (MODE == PJ_R) {
+              const int k = b.iters[sl];
+              const C* cpo = reinterpret_cast<const C*>(b.c_p) + ((size_t)(k & 1) * b.nslots + sl) * J.n_proj;
+              C* cpn = reinterpret_cast<C*>(b.c_p) + ((size_t)((k + 1) & 1) * b.nslots + sl) * J.n_proj;
+              C* cen = reinterpret_cast<C*>(b.c_e) + (size_t)sl * b.ce_stride;
+              C c = cr;
+              if (k > 0) c = cfma(from64<C>(b.beta_cur[sl]), cpo[p0 + p], c);
+              cpn[p0 + p] = c;
+              const CT e = (CT)J.ekb[p0 + p];
+              cen[p0 + p] = mk2(e * c.x, e * c.y);
+              const double cx = c.x, cy = c.y, e64 = J.ekb[p0 + p];
+              mu_g.x -= e64 * (cx * cx - cy * cy);
+              mu_g.y -= e64 * (2.0 * cx * cy);
+            }
+          }
         }
       }
+      if (MODE == PJ_R && threadIdx.x == 0) b.mu_part[(size_t)sl * b.PA + J.nA + g] = mu_g;
     }
   }  // list entries
 }
@@ -679,13 +716,13 @@ cudaError_t launch_op_tma(int mode, bool fp32, int R, dim3 grid, int threads, si
 size_t op_tma_smem_bytes(bool fp32, int mode, int R, int nx, int ny, int n_proj) {
   const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
   const size_t nin = mode == OP_COCG ? 2 : 1;
-  return el * (kStages * nin * (size_t)nx * ny + 2 * (size_t)(nx + 2 * R) * (ny + 2 * R) + (size_t)n_proj) +
+  return el * (kStages * nin * (size_t)nx * ny + 2 * (size_t)(nx + 2 * R) * (ny + 2 * R) + (size_t)n_proj + kCePad) +
          16 + 8 * kStages;
 }
 
 size_t op_smem_bytes(bool fp32, int mode, int R, int TY, int nx, int n_proj) {
   const size_t el = (mode == OP_RESID || !fp32) ? sizeof(double2) : sizeof(float2);
-  return el * (2 * (size_t)(TY + 2 * R) * (nx + 2 * R) + (size_t)n_proj);
+  return el * (2 * (size_t)(TY + 2 * R) * (nx + 2 * R) + (size_t)n_proj + kCePad);
 }
 
 cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
