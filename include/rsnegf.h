@@ -229,9 +229,10 @@ rsn_status rsn_autotune(rsn_ctx* ctx, int precision, int nslots, int* TY, int* L
    plane per CTA, Lz planes per CTA along z, ppt owned points per thread
    (1..4), or ppt = -1 for the plane-streaming (bulk-copy) kernel on whole
    planes (FP32 operator, planes of at most 1024 points with 16-byte aligned
-   sizes; other cases keep the register kernel).  Used by the autotuner and by
-   tests that force ragged tiles; it does not change results beyond rounding
-   order.  Errors: RSN_EINVAL. */
+   sizes; other cases keep the register kernel).  The FP64 true-residual
+   kernel takes TY and ppt but always works on two planes per CTA.  Used by
+   the autotuner and by tests that force ragged tiles; it does not change
+   results beyond rounding order.  Errors: RSN_EINVAL. */
 rsn_status rsn_set_tiling(rsn_ctx* ctx, int TY, int Lz, int ppt);
 
 /* Human-readable description of the context's last error ("" if none).

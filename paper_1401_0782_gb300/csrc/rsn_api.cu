@@ -111,7 +111,8 @@ struct rsn_ctx {
   bool dirty = true;
 
   // device operator data
-  DevBuf dg64, dg32, gld, L_idx, L_gam, inv_ptr, inv_p0, inv_q64, inv_q32;
+  DevBuf dg64, dg32, gld, L_idx, L_gam, inv_ptr, inv_p0, inv_q64, inv_q32, sup_pts;
+  int n_sup = 0;
   DevBuf grp_ptr, grp_p0, grp_np, grp_voff, grp_idx, grp_val64, grp_val32, ekb;
   int n_groups = 0, nL = 0, max_np = 1;
   JuncDev jh{};
@@ -207,9 +208,13 @@ static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslo
   t.threads = threads;
   int want = 8 * 152;
   int zt = (want + nslots * t.ytiles - 1) / (nslots * t.ytiles);
-  if (mode == OP_RESID) zt = nz;  // few systems need a true residual at a time: spread each over many CTAs
   zt = std::max(1, std::min(zt, std::max(1, nz / (2 * R + 2))));
   if (c->tile_override[1] > 0) zt = (nz + c->tile_override[1] - 1) / c->tile_override[1];
+  // few systems need a true residual at a time and it sits on every
+  // iteration's critical path: two planes per CTA whatever the operator
+  // tiling, so that each CTA marches through 2R + 2 planes only (latency, not
+  // bandwidth, bounds it)
+  if (mode == OP_RESID) zt = std::max(1, nz / 2);
   t.Lz = (nz + zt - 1) / zt;
   t.ztiles = (nz + t.Lz - 1) / t.Lz;
   t.n = t.ytiles * t.ztiles;
@@ -308,7 +313,12 @@ static rsn_status commit_setup(rsn_ctx* c) {
   const int G = c->n_groups;
   for (int g = 0; g < G; ++g)
     for (int k = gptr[g]; k < gptr[g + 1]; ++k) cnt[gidx[k] + 1]++;
-  for (long long i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> sup;  // grid points inside at least one projector support
+  for (long long i = 0; i < N; ++i) {
+    if (cnt[i + 1] > 0) sup.push_back((int)i);
+    cnt[i + 1] += cnt[i];
+  }
+  c->n_sup = (int)sup.size();
   const size_t nent = (size_t)cnt[N];
   std::vector<int> ip0(std::max<size_t>(1, nent)), fill(cnt.begin(), cnt.end() - 1);
   std::vector<double> iq64(std::max<size_t>(1, nent) * 4 * nq, 0.0);
@@ -330,6 +340,7 @@ static rsn_status commit_setup(rsn_ctx* c) {
   };
   RSN_CUDA(c, up(c->inv_ptr, cnt.data(), (N + 1) * sizeof(int)));
   RSN_CUDA(c, up(c->inv_p0, ip0.data(), nent * sizeof(int)));
+  RSN_CUDA(c, up(c->sup_pts, sup.data(), sup.size() * sizeof(int)));
   RSN_CUDA(c, up(c->inv_q64, iq64.data(), nent * 4 * nq * sizeof(double)));
   RSN_CUDA(c, up(c->inv_q32, iq32.data(), nent * 4 * nq * sizeof(float)));
   RSN_CUDA(c, up(c->grp_ptr, gptr.data(), gptr.size() * sizeof(int)));
@@ -366,6 +377,9 @@ static rsn_status commit_setup(rsn_ctx* c) {
   J.inv_p0 = c->inv_p0.as<int>();
   J.inv_q64 = c->inv_q64.as<double2>();
   J.inv_q32 = c->inv_q32.as<float4>();
+  J.sup_pts = c->sup_pts.as<int>();
+  J.n_sup = c->n_sup;
+  J.nS = (c->n_sup + kVecPts - 1) / kVecPts;
   J.grp_ptr = c->grp_ptr.as<int>();
   J.grp_p0 = c->grp_p0.as<int>();
   J.grp_np = c->grp_np.as<int>();
@@ -909,13 +923,14 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
                                     bdev, nullptr, nullptr, nullptr);
       if (e != cudaSuccess) return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 1], st, evf)) != cudaSuccess) return e;
+      if (proj && (e = launch_qproj(fp32, S, c->jh.nS, st, ji, bdev)) != cudaSuccess) return e;
       if ((e = launch_cocg_update(fp32, S, nB, st, ji, bdev)) != cudaSuccess) return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 2], st, evf)) != cudaSuccess) return e;
       if ((e = launch_book(S, it, st, ji, bdev)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
-  const int per_iter = proj ? 11 : 9;
+  const int per_iter = proj ? 12 : 9;
   const double vbytes = (double)N * (fp32 ? sizeof(float2) : sizeof(double2));
   cudaGraphExec_t gexec = nullptr;
   if (o->use_graph) {

@@ -60,6 +60,8 @@ struct JuncDev {
   const int* inv_p0;
   const double2* inv_q64;
   const float4* inv_q32;
+  const int* sup_pts;  // the grid points with at least one entry, ascending
+  int n_sup, nS;       // their number; CTAs per slot of the projector-term kernel
   const int* grp_ptr;
   const int* grp_p0;
   const int* grp_np;
@@ -180,6 +182,7 @@ cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, cons
                             const BatchDev* b);
 cudaError_t launch_emit(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_list(cudaStream_t st, const BatchDev* b);
+cudaError_t launch_qproj(bool fp32, int nslots, int nS, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_t_final(int n_e, int n_cols, cudaStream_t st, const double* t_all,
                            const double* gr_cols, double* T_out);
 cudaError_t launch_grad_sys(int nsys, long long N, cudaStream_t st, const double2* lam, const double2* x,

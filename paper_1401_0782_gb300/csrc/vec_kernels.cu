@@ -133,23 +133,11 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
   C* dv = reinterpret_cast<C*>(b.d);
   const long long i0 = (long long)blockIdx.x * kVecPts;
   const long long i1 = min(i0 + (long long)kVecPts, J.N);
-  // the operator kernel leaves out the projector term of q = A p: it is added
-  // here, q(i) -= sum over the atom entries of i of v_p(i) e_kb[p] c_p, with
-  // e_kb c_p of the new direction from the operator kernel (zero-padded)
-  const int n_proj = J.n_proj, nq = J.inv_nq;
-  const C* cen = reinterpret_cast<const C*>(b.c_e) + (size_t)s * b.ce_stride;
   T nrm = 0, rre = 0, rim = 0;
   for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
     const long long g = vo + i;
     const C p = pn[g];
-    C q = qv[g];
-    if (n_proj > 0) {
-      const int e0 = J.inv_ptr[i], e1 = J.inv_ptr[i + 1];
-      for (int e = e0; e < e1; ++e) {
-        const C* cp = cen + J.inv_p0[e];
-        for (int qd = 0; qd < nq; ++qd) q = proj_quad<C, T>(J, e * nq + qd, cp + 4 * qd, q);
-      }
-    }
+    const C q = qv[g];
     C r = rv[g];
     r.x -= alpha.x * q.x - alpha.y * q.y;
     r.y -= alpha.x * q.y + alpha.y * q.x;
@@ -316,6 +304,45 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
       if (MODE == PJ_R && threadIdx.x == 0) b.mu_part[(size_t)sl * b.PA + J.nA + g] = mu_g;
     }
   }  // list entries
+}
+
+// ---------------------------------------------------------------------------
+// Projector term of q = A p (the operator kernel leaves it out): for the grid
+// points inside a projector support, q(i) -= sum over the atom entries of i of
+// v_p(i) e_kb[p] c_p, with e_kb c_p of the new direction from the projection
+// kernel (zero-padded after the last projector).  ACTIVE slots.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) qproj_kernel(const JuncDev* __restrict__ jt,
+                                                            const BatchDev* __restrict__ bp) {
+  using C = typename cx<T>::t;
+  const BatchDev& b = *bp;
+  const int s = blockIdx.y;
+  if (b.state[s] != SL_ACTIVE) return;
+  const JuncDev& J = jt[b.junc[s]];
+  if ((int)blockIdx.x >= J.nS) return;
+  const int nq = J.inv_nq;
+  const C* cen = reinterpret_cast<const C*>(b.c_e) + (size_t)s * b.ce_stride;
+  C* qv = reinterpret_cast<C*>(b.q) + b.voff[s];
+  const int k0 = blockIdx.x * kVecPts, k1 = min(k0 + kVecPts, J.n_sup);
+  for (int k = k0 + threadIdx.x; k < k1; k += kVecThreads) {
+    const int i = J.sup_pts[k];
+    const int e0 = J.inv_ptr[i], e1 = J.inv_ptr[i + 1];
+    C q = qv[i];
+    for (int e = e0; e < e1; ++e) {
+      const C* cp = cen + J.inv_p0[e];
+      for (int qd = 0; qd < nq; ++qd) q = proj_quad<C, T>(J, e * nq + qd, cp + 4 * qd, q);
+    }
+    qv[i] = q;
+  }
+}
+
+cudaError_t launch_qproj(bool fp32, int nslots, int nS, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
+  if (nS <= 0) return cudaSuccess;
+  dim3 grid(nS, nslots);
+  if (fp32) qproj_kernel<float><<<grid, kVecThreads, 0, st>>>(jt, b);
+  else qproj_kernel<double><<<grid, kVecThreads, 0, st>>>(jt, b);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
