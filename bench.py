@@ -40,6 +40,13 @@ WORKLOAD = ("junction 24x24x120 (N=69,120), h=0.35, 8th-order FD, 20 atoms x 4 K
 CPU_SAMPLE_RTOL = 1e-10
 
 
+
+# DRAM bytes per algorithmic byte of the COCG operator kernel, from one ncu
+# capture (python -m paper_1401_0782_gb300.kernel_bench --kind op --slots 256
+# --reps 3; dram__bytes_read.sum + dram__bytes_write.sum = 557.6 MB against
+# 566.2 MB algorithmic).  Taken again whenever that kernel changes.
+OP_DRAM_PER_ALG_BYTE = 557.584128 / 566.23104
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -319,13 +326,19 @@ def run_ours(args):
             },
             "roofline": {
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "kernel": "op_kernel<float,4,*,OP_COCG> (fused p-update + 25-point stencil + V/CAP + projectors + p^T q)",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (OP_DRAM_PER_ALG_BYTE * kb / klaunch) if klaunch else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch with 256 active "
+                                  "slots (0.985 of its algorithmic bytes), scaled to this run's mean launch",
+                "kernel": "op_kernel<float,4,*,OP_COCG> (fused p-update + 25-point stencil + V/CAP + p^T A p; "
+                          "the projector term of A p is added by the support-point kernel)",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                                "fallback 6.8 TB/s",
                 "algorithmic_bytes": "32 B per active system per grid point (read r, p_old; write p_new, q)",
                 "launches_timed": klaunch, "kernel_ms": kms,
                 "update_kernel_gbs": upd,
+                "update_kernel_note": "projector-term kernel on the support points + COCG update, "
+                                      "6 vectors x 8 B per point algorithmic",
             },
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "steps": e2e_steps},
