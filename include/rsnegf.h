@@ -187,10 +187,10 @@ rsn_status rsn_transmission_vjp(rsn_ctx* ctx, int n_e, const double* E, int n_co
 /* Counters of the last solve on this context: total Krylov iterations over all
    systems, true-residual replacements (reliable updates), device kernel
    launches queued, elapsed GPU milliseconds of the solve phase, and the number
-   of systems that RSN_MIXED handed to FP64 because the FP32 recurrence stalled
-   (a near-singular A(E): the FP32 operator error times the condition number
-   approaches 1; such systems continue in FP64 from their iterate where it is
-   kept).  Any pointer may be NULL. */
+   of systems that RSN_MIXED solved again in FP64 because the FP32 recurrence
+   stalled (a near-singular A(E): the FP32 operator error times the condition
+   number approaches 1) or because the mixed pass stopped early when most of
+   its finished systems had stalled.  Any pointer may be NULL. */
 rsn_status rsn_last_stats(const rsn_ctx* ctx, int64_t* krylov_iters, int64_t* sweeps,
                           int64_t* launches, double* gpu_ms, int64_t* fp64_fallbacks);
 
