@@ -172,6 +172,24 @@ rsn_status rsn_solve_columns(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
 rsn_status rsn_transmission(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
                             const int32_t* cols, const rsn_solver_opts* opts, double* T);
 
+/* T(E) of several junctions at once (many junctions, energies and column sets
+   of uneven sizes; each junction is Eq. T-realspace on its own context):
+   ctxs[k] holds junction k (distinct contexts, all set up); it gets n_e[k]
+   energies E[k] and n_cols[k] columns cols[k], and T[k] (host, n_e[k] doubles)
+   receives its T as rsn_transmission would.  Each context solves on its own
+   stream from its own host thread, so the junctions share the GPU through
+   concurrent streams; when opts->rhs_block is 0, each context's slot pool is
+   capped by its share of the free device memory.  opts may be NULL (RSN_MIXED
+   defaults).  status (n_ctx entries, may be NULL) receives each junction's
+   result; the call returns RSN_OK if all succeeded, else the first failing
+   junction's status (its message is in rsn_last_error(ctxs[k])).
+   Errors: RSN_EINVAL (NULL arrays, a repeated context); as rsn_transmission per
+   junction.  The paper treats one junction at a time; batching is this
+   library's. */
+rsn_status rsn_batch_transmission(int n_ctx, rsn_ctx* const* ctxs, const int* n_e, const double* const* E,
+                                  const int* n_cols, const int32_t* const* cols, const rsn_solver_opts* opts,
+                                  double* const* T, rsn_status* status);
+
 /* Vector-Jacobian product of T with respect to V_loc:
    dV[r] = sum_e T_bar[e] dT(E[e])/dV_loc(r)
          = sum_e T_bar[e] 8 sum_c Gamma_R,c Re(lambda_{e,c}(r) x_{e,c}(r)),

@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes as ct
 import dataclasses
 import os
-from typing import Optional, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -39,6 +39,8 @@ _SIGS = {
                                     ct.c_void_p]),
     "rsn_transmission_vjp": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
                                         ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "rsn_batch_transmission": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                          ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_last_stats": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_last_error": (ct.c_char_p, [ct.c_void_p]),
     "rsn_kernel_stats": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -269,3 +271,38 @@ class Context:
                                                               ct.byref(ms), ct.byref(fb)))
         return {"krylov_iters": it.value, "sweeps": sw.value, "launches": la.value, "gpu_ms": ms.value,
                 "fp64_fallbacks": fb.value}
+
+
+def batch_transmission(contexts: Sequence["Context"], energies: Sequence[Sequence[float]],
+                       cols: Optional[Sequence[Optional[Sequence[int]]]] = None,
+                       opts: Optional[SolverOpts] = None) -> List[np.ndarray]:
+    """T(E) of several junctions at once (``rsn_batch_transmission``).
+
+    ``contexts[k]`` holds junction k; it gets ``energies[k]`` and ``cols[k]``
+    (default: its right-lead columns).  Returns one T array per junction;
+    raises RsnError naming the first junction that failed.
+    """
+    lib = load()
+    n = len(contexts)
+    if len(energies) != n or (cols is not None and len(cols) != n):
+        raise ValueError("one energy list and one column list per context")
+    opts = opts or default_opts(RSN_MIXED)
+    Es = [np.ascontiguousarray(e, dtype=np.float64) for e in energies]
+    Cs = [np.ascontiguousarray(ctx.junction.right_columns() if (cols is None or cols[k] is None) else cols[k],
+                               dtype=np.int32) for k, ctx in enumerate(contexts)]
+    Ts = [np.zeros(e.size, np.float64) for e in Es]
+    ctxs = (ct.c_void_p * max(n, 1))(*[c.h.value for c in contexts])
+    n_e = (ct.c_int * max(n, 1))(*[e.size for e in Es])
+    n_c = (ct.c_int * max(n, 1))(*[c.size for c in Cs])
+    Ep = (ct.c_void_p * max(n, 1))(*[_ptr(e) for e in Es])
+    Cp = (ct.c_void_p * max(n, 1))(*[_ptr(c) for c in Cs])
+    Tp = (ct.c_void_p * max(n, 1))(*[_ptr(t) for t in Ts])
+    st = (ct.c_int * max(n, 1))()
+    rc = lib.rsn_batch_transmission(n, ctxs, n_e, Ep, n_c, Cp, ct.byref(opts), Tp, st)
+    if rc != RSN_OK:
+        bad = [k for k in range(n) if st[k] != RSN_OK]
+        k = bad[0] if bad else 0
+        msg = lib.rsn_last_error(contexts[k].h).decode() if n else ""
+        raise RsnError("rsn_batch_transmission", rc, f"junction {k}: {msg}")
+    return Ts
+

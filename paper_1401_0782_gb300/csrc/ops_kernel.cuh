@@ -414,7 +414,13 @@ cudaError_t launch_op_r(int mode, bool fp32, int ppt, dim3 grid, int threads, si
   }
 #undef RSN_PICK
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the device's opt-in maximum, not this launch's size: contexts on other
+    // host threads may launch the same kernel with other sizes concurrently
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((size_t)optin < smem) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
   }
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -629,7 +635,13 @@ cudaError_t launch_op_tma_r(int mode, bool fp32, dim3 grid, int threads, size_t 
   else if (mode == OP_APPLY) kern = fp32 ? op_kernel_tma<float, R, OP_APPLY> : op_kernel_tma<double, R, OP_APPLY>;
   else return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the device's opt-in maximum, not this launch's size: contexts on other
+    // host threads may launch the same kernel with other sizes concurrently
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((size_t)optin < smem) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
   }
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);

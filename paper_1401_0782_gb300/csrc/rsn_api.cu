@@ -18,6 +18,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1368,6 +1369,87 @@ rsn_status rsn_transmission_vjp(rsn_ctx* c, int n_e, const double* E, int n_cols
   if (!c) return RSN_EINVAL;
   if (!dV) RSN_FAIL(c, RSN_EINVAL, "dV is NULL");
   return transmission_impl(c, n_e, E, n_cols, cols, o, T_bar, dV, dV_is_device, T);
+}
+
+rsn_status rsn_batch_transmission(int n_ctx, rsn_ctx* const* ctxs, const int* n_e, const double* const* E,
+                                  const int* n_cols, const int32_t* const* cols, const rsn_solver_opts* opts,
+                                  double* const* T, rsn_status* status) {
+  if (n_ctx < 0) return RSN_EINVAL;
+  if (n_ctx == 0) return RSN_OK;
+  if (!ctxs || !n_e || !E || !n_cols || !cols || !T) return RSN_EINVAL;
+  for (int k = 0; k < n_ctx; ++k) {
+    if (!ctxs[k]) return RSN_EINVAL;
+    for (int l = 0; l < k; ++l)
+      if (ctxs[l] == ctxs[k]) RSN_FAIL(ctxs[k], RSN_EINVAL, "context %d repeats context %d", k, l);
+  }
+  rsn_solver_opts base;
+  if (opts) base = *opts;
+  else rsn_default_opts(RSN_MIXED, &base);
+  // per-context options: without an explicit slot count, each context's pool
+  // is capped by its share of the free memory of its device
+  std::vector<rsn_solver_opts> ok(n_ctx, base);
+  std::map<int, int> per_dev;
+  for (int k = 0; k < n_ctx; ++k) per_dev[ctxs[k]->device]++;
+  std::map<int, size_t> free_dev;
+  for (auto& d : per_dev) {
+    size_t fr = 0, tot = 0;
+    if (cudaSetDevice(d.first) == cudaSuccess && cudaMemGetInfo(&fr, &tot) == cudaSuccess) free_dev[d.first] = fr;
+    else free_dev[d.first] = 0;
+  }
+  if (base.rhs_block <= 0) {
+    for (int k = 0; k < n_ctx; ++k) {
+      rsn_ctx* c = ctxs[k];
+      const double share = 0.6 * (double)free_dev[c->device] / per_dev[c->device];
+      const long long cap = (long long)(share / (double)slot_bytes(c, base.precision == RSN_MIXED));
+      ok[k].rhs_block = (int)std::max<long long>(1, std::min<long long>(cap, 2048));
+    }
+  }
+  // order each context's work after its caller's stream once, up front, and
+  // let the per-call stream handshake use the context's own stream: contexts
+  // that share a caller stream (one framework stream) then do not wait for
+  // one another; the caller's streams wait for the results at the end
+  std::vector<cudaStream_t> user(n_ctx);
+  for (int k = 0; k < n_ctx; ++k) {
+    rsn_ctx* c = ctxs[k];
+    RSN_CUDA(c, cudaSetDevice(c->device));
+    RSN_CUDA(c, cudaEventRecord(c->ev_in, c->user_stream));
+    RSN_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_in, 0));
+  }
+  for (int k = 0; k < n_ctx; ++k) {
+    user[k] = ctxs[k]->user_stream;
+    ctxs[k]->user_stream = ctxs[k]->st;
+  }
+  std::vector<rsn_status> st(n_ctx, RSN_OK);
+  std::vector<std::thread> th;
+  th.reserve(n_ctx);
+  for (int k = 0; k < n_ctx; ++k)
+    th.emplace_back([&, k]() {
+      cudaSetDevice(ctxs[k]->device);  // a new host thread starts on device 0
+      if (n_e[k] > 0 && !T[k]) {
+        st[k] = RSN_EINVAL;
+        ctxs[k]->err = "T is NULL";
+        return;
+      }
+      st[k] = transmission_impl(ctxs[k], n_e[k], E[k], n_cols[k], cols[k], &ok[k], nullptr, nullptr, 0, T[k]);
+    });
+  for (auto& t : th) t.join();
+  for (int k = 0; k < n_ctx; ++k) {
+    rsn_ctx* c = ctxs[k];
+    c->user_stream = user[k];
+    if (cudaSetDevice(c->device) != cudaSuccess || cudaEventRecord(c->ev_out, c->st) != cudaSuccess ||
+        cudaStreamWaitEvent(c->user_stream, c->ev_out, 0) != cudaSuccess) {
+      if (st[k] == RSN_OK) {
+        st[k] = RSN_ECUDA;
+        c->err = "rsn_batch_transmission: ordering the caller's stream after the context failed";
+      }
+    }
+  }
+  rsn_status worst = RSN_OK;
+  for (int k = 0; k < n_ctx; ++k) {
+    if (status) status[k] = st[k];
+    if (worst == RSN_OK && st[k] != RSN_OK) worst = st[k];
+  }
+  return worst;
 }
 
 // One kernel of the COCG iteration in isolation: every slot ACTIVE with a

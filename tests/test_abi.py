@@ -54,6 +54,11 @@ def test_null_context_and_create_errors(lib):
     assert rc in (B.RSN_ECUDA, B.RSN_EINVAL)
     assert h.value is None
     assert len(lib.rsn_last_error(None)) > 0
+    # the batched entry point checks its arrays before touching a device
+    assert lib.rsn_batch_transmission(0, None, None, None, None, None, None, None, None) == B.RSN_OK
+    assert lib.rsn_batch_transmission(-1, None, None, None, None, None, None, None, None) == B.RSN_EINVAL
+    assert lib.rsn_batch_transmission(2, None, None, None, None, None, None, None, None) == B.RSN_EINVAL
+    assert B.batch_transmission([], [], []) == []
 
 
 def test_package_import_loads_nothing():
