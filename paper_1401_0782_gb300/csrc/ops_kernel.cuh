@@ -491,15 +491,13 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
   } else {
     src0 = reinterpret_cast<const C*>(x_in) + vo;
   }
-  // COCG: no coefficients, the projector term of q is added by the update kernel
+  // APPLY only: in COCG the projector term of q is added on the support points
   if (MODE != OP_COCG && n_proj > 0) {
-    {
-      const C* cin = reinterpret_cast<const C*>(c_in) + (size_t)s * n_proj;
-      for (int p = tid; p < n_proj; p += nt) {
-        const T e = (T)J.ekb[p];
-        const C c = cin[p];
-        ce[p] = mk2(e * c.x, e * c.y);
-      }
+    const C* cin = reinterpret_cast<const C*>(c_in) + (size_t)s * n_proj;
+    for (int p = tid; p < n_proj; p += nt) {
+      const T e = (T)J.ekb[p];
+      const C c = cin[p];
+      ce[p] = mk2(e * c.x, e * c.y);
     }
     for (int p = tid; p < kCePad; p += nt) ce[n_proj + p] = czero<C>();
   }
