@@ -24,6 +24,9 @@ checked by eye against the paper:
 * ``transmission``         -- Eq. T-realspace with the CAP as coupling:
                               T = 4 sum_{i in L, j in R} Gamma_L,i Gamma_R,j |G_ij|^2
                               (factor 4: the coupling is Gamma_std = 2*CAP).
+* ``shifted_cocg``         -- columns at every energy of a window from one Krylov
+                              space (A(E) is a shift family, Eq. G): COCG on a seed
+                              energy plus the collinear shifted recurrences.
 * ``transmission_grad``    -- dT/dV_loc by the adjoint identity
                               dG/dV_r = G e_r e_r^T G (G = G^T, Eq. complex-sym).
 * ``transmission_trace``   -- Eq. T written as a dense trace, Tr{G Gam_R G^dag Gam_L}.
@@ -58,6 +61,7 @@ __all__ = [
     "transmission",
     "column_weights",
     "transmission_grad",
+    "shifted_cocg",
     "transmission_trace",
     "transmission_eigen",
     "open_channels",
@@ -301,6 +305,70 @@ def transmission(j, energies: Iterable[float], cols: Optional[Sequence[int]] = N
         X = solve_columns(j, float(E), cols, method=method)
         out.append(4.0 * np.sum(j.gamma_r[cols] * column_weights(j, X)))
     return np.asarray(out)
+
+
+def shifted_cocg(j, energies: Sequence[float], b: np.ndarray, seed: int = 0, rtol: float = 1e-10,
+                 maxiter: int = 50000, stop_at: Optional[int] = None):
+    """x(E) = A(E)^{-1} b for every E of ``energies`` from one Krylov space.
+
+    A(E) = E 1 - H_KS + i Gamma (Eq. G) is a shift family: A(E) = A(E_s) +
+    (E - E_s) 1 around the seed energy E_s = energies[seed].  The seed system
+    runs plain COCG (x_0 = 0):
+
+        alpha_k = rho_k / (p_k^T A_s p_k),  x += alpha_k p_k,  r -= alpha_k A_s p_k,
+        beta_k = rho_{k+1} / rho_k,         p_{k+1} = r_{k+1} + beta_k p_k.
+
+    Its residual is r_k = R_k(A_s) b with R_k a polynomial, R_k(0) = 1.  The
+    shifted system's residual in the same Krylov space is collinear with it,
+    r^sig_k = r_k / pi_k with pi_k = R_k(-sig), sig = E - E_s.  The three-term
+    recurrence of R_k evaluated at -sig gives (alpha_{-1} = 1, beta_{-1} = 0,
+    pi_{-1} = pi_0 = 1):
+
+        pi_{k+1} = (1 + alpha_k sig) pi_k + (alpha_k beta_{k-1} / alpha_{k-1}) (pi_k - pi_{k-1}),
+        alpha^sig_k = alpha_k pi_k / pi_{k+1},   beta^sig_k = beta_k (pi_k / pi_{k+1})^2,
+        x^sig += alpha^sig_k p^sig_k,            p^sig_{k+1} = r_{k+1} / pi_{k+1} + beta^sig_k p^sig_k.
+
+    One operator application per iteration serves every energy.  Iterates until
+    every shifted residual ||r_k|| / |pi_k| is at most rtol ||b|| (or for
+    ``stop_at`` iterations).  Returns (X, iterations, pi, r): X[e] the solution at
+    energies[e], pi[e] the collinearity factor and r the seed residual at the stop.
+    """
+    E = np.asarray(energies, dtype=float)
+    Es = float(E[seed])
+    sig = E - Es
+    b = np.asarray(b, dtype=np.complex128)
+    bn = np.linalg.norm(b)
+    nE = E.size
+    X = np.zeros((nE, b.size), dtype=np.complex128)
+    pi = np.ones(nE, dtype=np.complex128)
+    if bn == 0.0:
+        return X, 0, pi, b.copy()
+    Hloc = local_hamiltonian(j)
+    r = b.copy()
+    P = np.repeat(r[None, :], nE, axis=0)  # p^sig_0 = r_0 / pi_0 = b
+    pi_old = np.ones(nE, dtype=np.complex128)
+    rho = r @ r
+    alpha_old, beta_old = 1.0 + 0j, 0j
+    k = 0
+    limit = maxiter if stop_at is None else stop_at
+    while k < limit:
+        p = P[seed]
+        q = apply_operator(j, Es, p, Hloc)
+        alpha = rho / (p @ q)
+        r = r - alpha * q
+        rho_new = r @ r
+        beta = rho_new / rho
+        pi_new = (1.0 + alpha * sig) * pi + (alpha * beta_old / alpha_old) * (pi - pi_old)
+        a_sig = alpha * pi / pi_new
+        b_sig = beta * (pi / pi_new) ** 2
+        X += a_sig[:, None] * P
+        P = r[None, :] / pi_new[:, None] + b_sig[:, None] * P
+        pi_old, pi = pi, pi_new
+        alpha_old, beta_old, rho = alpha, beta, rho_new
+        k += 1
+        if stop_at is None and np.max(np.linalg.norm(r) / np.abs(pi)) <= rtol * bn:
+            break
+    return X, k, pi, r
 
 
 def transmission_grad(j, energies: Sequence[float], cols: Optional[Sequence[int]] = None,

@@ -270,3 +270,69 @@ def test_gradient_pin_catches_wrong_adjoint_weight():
     g_wrong = 8.0 * np.sum(j.gamma_r[cols][None, :] * np.real(np.conj(Lam) * X), axis=1)
     _, g = O.transmission_grad(j, [E])
     assert np.abs(g_wrong - g).max() > 1e-3 * np.abs(g).max()
+
+
+# ----------------------------------------------------------------------------
+# shifted COCG over an energy window (A(E) is a shift family, Eq. G)
+# ----------------------------------------------------------------------------
+
+def _shift_junction():
+    return P.molecular_junction(seed=12, nx=10, ny=10, nz=30, n_wells=3, n_cap=4)
+
+
+def test_shifted_cocg_matches_lu_at_every_energy():
+    j = _shift_junction()
+    E = np.linspace(0.15, 0.35, 5)
+    col = int(j.right_columns()[17])
+    b = np.zeros(j.N, complex)
+    b[col] = 1.0
+    for seed in (0, 2):
+        X, iters, _, _ = O.shifted_cocg(j, E, b, seed=seed, rtol=1e-12)
+        assert 0 < iters < 5000
+        for e, En in enumerate(E):
+            ref = O.solve_columns(j, En, [col])[:, 0]
+            assert np.linalg.norm(X[e] - ref) <= 1e-9 * np.linalg.norm(ref), (seed, En)
+            # the true residual at each energy, with the oracle's own operator
+            res = np.linalg.norm(b - O.apply_operator(j, En, X[e]))
+            assert res <= 1e-11, (seed, En, res)
+
+
+def test_shifted_cocg_residuals_stay_collinear():
+    # mid-iteration, each energy's true residual is the seed residual over pi
+    j = _shift_junction()
+    E = np.array([0.2, 0.12, 0.31])
+    b = np.zeros(j.N, complex)
+    b[int(j.right_columns()[5])] = 1.0
+    X, iters, pi, r = O.shifted_cocg(j, E, b, seed=0, stop_at=25)
+    assert iters == 25 and pi[0] == 1.0
+    for e, En in enumerate(E):
+        true_r = b - O.apply_operator(j, En, X[e])
+        assert np.linalg.norm(true_r - r / pi[e]) <= 1e-9 * np.linalg.norm(true_r), En
+    # the seed itself is plain COCG: 25 steps of the oracle's own recurrence
+    x = np.zeros(j.N, complex)
+    rr = b.copy()
+    p = rr.copy()
+    rho = rr @ rr
+    for _ in range(25):
+        q = O.apply_operator(j, 0.2, p)
+        a = rho / (p @ q)
+        x += a * p
+        rr -= a * q
+        rho_new = rr @ rr
+        p = rr + (rho_new / rho) * p
+        rho = rho_new
+    assert np.linalg.norm(X[0] - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_shifted_cocg_pin_catches_a_wrong_shift_sign():
+    # a plausible mistake: shifting by E_s - E instead of E - E_s.  Solving at the
+    # energies mirrored about the seed reproduces it, and the LU pin rejects it.
+    j = _shift_junction()
+    E = np.array([0.2, 0.26])
+    col = int(j.right_columns()[3])
+    b = np.zeros(j.N, complex)
+    b[col] = 1.0
+    mirrored = 2 * E[0] - E
+    X, _, _, _ = O.shifted_cocg(j, mirrored, b, seed=0, rtol=1e-12)
+    ref = O.solve_columns(j, E[1], [col])[:, 0]
+    assert np.linalg.norm(X[1] - ref) > 1e-3 * np.linalg.norm(ref)
