@@ -133,7 +133,9 @@ rsn_status rsn_set_cap(rsn_ctx* ctx, const double* gamma_l, const double* gamma_
 /* y_k = A(E_k) x_k for n_rhs vectors (the matvec of Eqs. G/Hop: FD stencil,
    V_loc, CAP and projectors).  x_dev, y_dev: device, [n_rhs][N] complex128
    (precision RSN_FP64) or complex64 (RSN_MIXED).  E: host, n_rhs doubles.
-   Errors: RSN_ESTATE, RSN_EINVAL, RSN_ECUDA. */
+   Errors: RSN_ESTATE, RSN_EINVAL (also n_rhs > 65535: split the call),
+   RSN_ECUDA.  On an error after work was queued, the caller's stream is still
+   ordered after that work. */
 rsn_status rsn_apply(rsn_ctx* ctx, int precision, int n_rhs, const double* E,
                      const void* x_dev, void* y_dev);
 
@@ -145,8 +147,8 @@ rsn_status rsn_apply(rsn_ctx* ctx, int precision, int n_rhs, const double* E,
    Its per-call scratch (launch descriptor, per-vector tables, projector
    coefficients) is a fixed 8 MiB device array that every device which loads
    the library holds until the process exits; a call whose scratch would not
-   fit (n_rhs * (24 + 16 * max(n_proj, 1)) bytes plus about 1 KiB) fails with
-   RSN_EINVAL.  The operator data must already be on the device: after the last
+   fit (n_rhs * (24 + 16 * max(n_proj, 1)) bytes plus about 1 KiB), or with
+   n_rhs > 65535, fails with RSN_EINVAL before anything is queued.  The operator data must already be on the device: after the last
    setter, make one allocating call (e.g. rsn_apply) first, else RSN_ESTATE.
    The first call on a device looks up the array's device address
    (cudaGetSymbolAddress), so make it before any stream capture.  All calls
@@ -234,23 +236,28 @@ rsn_status rsn_bench_kernel(rsn_ctx* ctx, int precision, int kind, int nslots, i
                             double* ms_per_launch, double* bytes_per_launch);
 
 /* Autotuner: times the fused operator kernel (rsn_bench_kernel kind 0) for a
-   set of tilings of this grid -- the plane-streaming (bulk-copy) kernel with
-   several z-chunk lengths, and the register-prefetch kernel over rows per tile,
-   points per thread and z-chunks -- and keeps the fastest on the context.
-   Outputs (any may be NULL): the chosen TY, Lz, ppt (0 = automatic), tma (1 if
-   the plane-streaming kernel won) and its algorithmic GB/s.  Errors: as
-   rsn_bench_kernel; RSN_ECUDA if no candidate ran. */
+   set of tilings of this grid -- the FP32 point-pair kernel and the
+   whole-plane bulk-copy kernel with several z-chunk lengths, and the
+   register-prefetch kernel over rows per tile, points per thread and z-chunks
+   -- and keeps the fastest on the context.  Outputs (any may be NULL): the
+   chosen TY, Lz, ppt (0 = automatic), tma (2: the point-pair kernel, 1: the
+   whole-plane bulk-copy kernel, 0: the register kernel) and its algorithmic
+   GB/s.  Errors: as rsn_bench_kernel; RSN_ECUDA if no candidate ran. */
 rsn_status rsn_autotune(rsn_ctx* ctx, int precision, int nslots, int* TY, int* Lz, int* ppt,
                         int* tma, double* best_gbs);
 
-/* Override the operator kernel's tile (0 = automatic): TY rows of the x-y
-   plane per CTA, Lz planes per CTA along z, ppt owned points per thread
-   (1..4), or ppt = -1 for the plane-streaming (bulk-copy) kernel on whole
-   planes (FP32 operator, planes of at most 1024 points with 16-byte aligned
-   sizes; other cases keep the register kernel).  The FP64 true-residual
-   kernel takes TY and ppt but always works on two planes per CTA.  Used by
-   the autotuner and by tests that force ragged tiles; it does not change
-   results beyond rounding order.  Errors: RSN_EINVAL. */
+/* Override the operator kernel's tile (0 = automatic).  Automatic: FP32
+   operators on grids with nx even and planes of at most 1280 points use the
+   point-pair kernel (two x-neighbours per thread, whole planes streamed by bulk
+   copies, Lz planes per CTA); everything else the register-prefetch kernel.
+   TY rows of the x-y plane per CTA and ppt owned points per thread (1..4)
+   select the register-prefetch kernel; ppt = -1 selects the whole-plane
+   bulk-copy kernel with one point per thread (FP32, planes of at most 1024
+   points with 16-byte aligned sizes; other cases keep the register kernel).
+   The FP64 true-residual kernel takes TY and ppt but always works on two
+   planes per CTA.  Used by the autotuner and by tests that force ragged
+   tiles; it does not change results beyond rounding order.
+   Errors: RSN_EINVAL. */
 rsn_status rsn_set_tiling(rsn_ctx* ctx, int TY, int Lz, int ppt);
 
 /* Human-readable description of the context's last error ("" if none).

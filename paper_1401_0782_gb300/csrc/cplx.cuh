@@ -68,4 +68,20 @@ __device__ __forceinline__ void block_sum(A (&v)[NV], double* red, double (&out)
   __syncthreads();
 }
 
+// Allow `smem` bytes of dynamic shared memory for kernel `kern`: the attribute
+// is set to the device's opt-in maximum less the kernel's static shared memory
+// (not to this launch's size: contexts on other host threads may launch the
+// same kernel with other sizes concurrently).
+inline cudaError_t set_max_dynamic_smem(const void* kern, size_t smem) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+  const long long room = (long long)optin - (long long)fa.sharedSizeBytes;
+  if (room < (long long)smem) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
+}
+
 }  // namespace rsn

@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "cplx.cuh"
+#include "ops_pair.cuh"
 #include "rsn_internal.h"
 #include "tma.cuh"
 
@@ -414,13 +415,7 @@ cudaError_t launch_op_r(int mode, bool fp32, int ppt, dim3 grid, int threads, si
   }
 #undef RSN_PICK
   if (smem > 48 * 1024) {
-    // the device's opt-in maximum, not this launch's size: contexts on other
-    // host threads may launch the same kernel with other sizes concurrently
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((size_t)optin < smem) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
   }
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -633,13 +628,7 @@ cudaError_t launch_op_tma_r(int mode, bool fp32, dim3 grid, int threads, size_t 
   else if (mode == OP_APPLY) kern = fp32 ? op_kernel_tma<float, R, OP_APPLY> : op_kernel_tma<double, R, OP_APPLY>;
   else return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
-    // the device's opt-in maximum, not this launch's size: contexts on other
-    // host threads may launch the same kernel with other sizes concurrently
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((size_t)optin < smem) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
   }
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -660,5 +649,10 @@ cudaError_t launch_op_tma_r(int mode, bool fp32, dim3 grid, int threads, size_t 
                                  cudaStream_t st, const JuncDev* jt, const BatchDev* b,         \
                                  const void* x_in, void* y_out, const void* c_in) {              \
     return launch_op_tma_r<R>(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);    \
+  }                                                                                               \
+  cudaError_t launch_op_pair_R##R(int mode, bool big, dim3 grid, int threads, size_t smem,        \
+                                  cudaStream_t st, const JuncDev* jt, const BatchDev* b,        \
+                                  const void* x_in, void* y_out, const void* c_in) {             \
+    return launch_op_pair_r<R>(mode, big, grid, threads, smem, st, jt, b, x_in, y_out, c_in);    \
   }                                                                                               \
   }

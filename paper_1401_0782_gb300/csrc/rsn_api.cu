@@ -60,7 +60,9 @@ struct DevBuf {
 struct Tiling {
   int TY = 0, Lz = 0, ytiles = 0, ztiles = 0, n = 0, ppt = 1, threads = 32;
   size_t smem = 0;
-  bool tma = false;  // whole-plane tile streamed by bulk copies (op_kernel_tma)
+  bool tma = false;   // whole-plane tile streamed by bulk copies (op_kernel_tma)
+  bool pair = false;  // FP32 point-pair kernel with plane streaming (op_pair_kernel)
+  bool big = false;   // its one-CTA-per-SM variant (planes of more than 2 * kPairThreads points)
 };
 
 // Slot pool of the streaming solver (sized for S slots of N points).
@@ -180,11 +182,41 @@ static void clear_graphs(rsn_ctx* c) {
 // ---------------------------------------------------------------------------
 // tiling of the operator kernel
 // ---------------------------------------------------------------------------
-static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslots) {
+// Tiling overrides (rsn_set_tiling): TY rows, Lz planes, ppt points per
+// thread; ppt = -1 selects the whole-plane bulk-copy kernel, ppt = -2 the FP32
+// point-pair kernel (also the automatic choice where it applies).
+// `streamable`: the vectors of this launch are 16-byte aligned (bulk copies).
+static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslots, bool streamable = true) {
   Tiling t;
   const int nx = c->nx, ny = c->ny, nz = c->nz, R = c->R;
-  // default: one point per thread (64 registers, 4 CTAs per SM), as many whole
-  // x rows per tile as fit 256 threads; the autotuner may choose otherwise
+  const long long pl = (long long)nx * ny;
+  // FP32 point-pair kernel: whole planes, nx even (16-byte pairs), at most
+  // 2 * kPairThreadsBig points per plane, no explicit register tile requested
+  const bool reg_forced = c->tile_override[0] > 0 || c->tile_override[2] > 0 || c->tile_override[3] == -1;
+  if (!compute64 && mode != OP_RESID && streamable && !reg_forced && nx % 2 == 0) {
+    const int thr = (int)(((pl / 2) + 31) / 32 * 32);
+    const size_t sm = op_pair_smem_bytes(mode, R, nx, ny, c->n_proj);
+    if (thr <= kPairThreadsBig && sm <= 200 * 1024) {
+      t.pair = true;
+      t.big = thr > kPairThreads;
+      t.threads = thr;
+      t.smem = sm;
+      t.TY = ny;
+      t.ytiles = 1;
+      t.ppt = 2;
+      const int per_sm = t.big ? 1 : 2;
+      int zt = (4 * per_sm * 152 + nslots - 1) / nslots;
+      zt = std::max(1, std::min(zt, std::max(1, nz / (2 * R + 2))));
+      if (c->tile_override[1] > 0) zt = (nz + c->tile_override[1] - 1) / c->tile_override[1];
+      t.Lz = (nz + zt - 1) / zt;
+      t.ztiles = (nz + t.Lz - 1) / t.Lz;
+      t.n = t.ztiles;
+      return t;
+    }
+  }
+  // register-prefetch kernel: one point per thread by default (64 registers,
+  // 4 CTAs per SM), as many whole x rows per tile as fit 256 threads; the
+  // autotuner may choose otherwise
   int TY = std::max(1, std::min(ny, 256 / std::max(1, nx)));
   {
     const int yt = (ny + TY - 1) / TY;
@@ -220,23 +252,32 @@ static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslo
   t.ztiles = (nz + t.Lz - 1) / t.Lz;
   t.n = t.ytiles * t.ztiles;
   t.smem = op_smem_bytes(!compute64, mode, R, TY, nx, c->n_proj);
-  // plane-streaming kernel: FP32 COCG / apply on whole planes whose byte sizes
-  // keep every bulk copy 16-byte aligned; an explicit TY or ppt selects the
-  // register-prefetch kernel instead
-  const long long pl = (long long)nx * ny;
-  if (!compute64 && mode != OP_RESID && pl <= 1024 && (pl * 8) % 16 == 0 && (c->N * 8) % 16 == 0 &&
+  // whole-plane bulk-copy kernel (on request): FP32 COCG / apply on planes
+  // whose byte sizes keep every bulk copy 16-byte aligned
+  if (!compute64 && mode != OP_RESID && streamable && pl <= 1024 && (pl * 8) % 16 == 0 && (c->N * 8) % 16 == 0 &&
       c->tile_override[3] == -1) {
-    t.TY = ny;
-    t.ytiles = 1;
-    t.n = t.ztiles;
     const size_t sm = op_tma_smem_bytes(true, mode, R, nx, ny, c->n_proj);
     if (sm <= 200 * 1024) {
+      t.TY = ny;
+      t.ytiles = 1;
+      t.n = t.ztiles;
       t.tma = true;
       t.smem = sm;
       t.threads = (int)((pl + 31) / 32 * 32);
     }
   }
   return t;
+}
+
+// Operator launch (COCG or apply) with a tiling from choose_tiling; the
+// JuncDev copy `jt` must carry the same tiling.
+static cudaError_t launch_inner(const rsn_ctx* c, const Tiling& t, int mode, bool fp32, int nslots, cudaStream_t st,
+                                const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out,
+                                const void* c_in) {
+  const dim3 grid(t.n, nslots);
+  if (t.pair) return launch_op_pair(mode, c->R, t.big, grid, t.threads, t.smem, st, jt, b, x_in, y_out, c_in);
+  if (t.tma) return launch_op_tma(mode, fp32, c->R, grid, t.threads, t.smem, st, jt, b, x_in, y_out, c_in);
+  return launch_op(mode, fp32, c->R, t.ppt, grid, t.threads, t.smem, st, jt, b, x_in, y_out, c_in);
 }
 
 // ---------------------------------------------------------------------------
@@ -405,9 +446,9 @@ struct LaunchCfg {
   const JuncDev* jt_resid;  // device pointer: tiling of the residual kernel
 };
 
-static rsn_status make_cfg(rsn_ctx* c, bool fp32, int nslots, LaunchCfg& cfg) {
-  cfg.inner = choose_tiling(c, !fp32, OP_COCG, nslots);
-  cfg.resid = choose_tiling(c, true, OP_RESID, nslots);
+static rsn_status make_cfg(rsn_ctx* c, const Tiling& inner, const Tiling& resid, LaunchCfg& cfg) {
+  cfg.inner = inner;
+  cfg.resid = resid;
   JuncDev js[2] = {c->jh, c->jh};
   for (int k = 0; k < 2; ++k) {
     const Tiling& t = k == 0 ? cfg.inner : cfg.resid;
@@ -422,6 +463,11 @@ static rsn_status make_cfg(rsn_ctx* c, bool fp32, int nslots, LaunchCfg& cfg) {
   cfg.jt_inner = c->jd.as<JuncDev>();
   cfg.jt_resid = c->jd.as<JuncDev>() + 1;
   return RSN_OK;
+}
+
+// the solver's tilings: COCG operator in the inner precision, FP64 true residual
+static rsn_status make_cfg(rsn_ctx* c, bool fp32, int nslots, LaunchCfg& cfg) {
+  return make_cfg(c, choose_tiling(c, !fp32, OP_COCG, nslots), choose_tiling(c, true, OP_RESID, nslots), cfg);
 }
 
 extern "C" {
@@ -892,7 +938,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   const int nB = c->jh.nB;
   const bool proj = c->n_proj > 0;
   const int KL = std::min(S, kListRows);
-  const dim3 gi(cfg.inner.n, S), gr(cfg.resid.n, KL);
+  const dim3 gr(cfg.resid.n, KL);
   const int G = std::max(1, std::min(kMaxGraphIters, o->graph_iters));
   const bool timing = o->timing != 0;
   while (timing && (int)c->tev.size() < 4 * G) {
@@ -918,10 +964,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       if (proj && (e = launch_project(0, fp32, S, c->n_groups, c->max_np, st, ji, bdev, nullptr, w.c_r.p)) != cudaSuccess)
         return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it], st, evf)) != cudaSuccess) return e;
-      e = cfg.inner.tma ? launch_op_tma(OP_COCG, fp32, c->R, gi, cfg.inner.threads, cfg.inner.smem, st, ji, bdev,
-                                        nullptr, nullptr, nullptr)
-                        : launch_op(OP_COCG, fp32, c->R, cfg.inner.ppt, gi, cfg.inner.threads, cfg.inner.smem, st, ji,
-                                    bdev, nullptr, nullptr, nullptr);
+      e = launch_inner(c, cfg.inner, OP_COCG, fp32, S, st, ji, bdev, nullptr, nullptr, nullptr);
       if (e != cudaSuccess) return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 1], st, evf)) != cudaSuccess) return e;
       if (proj && (e = launch_qproj(fp32, S, c->jh.nS, st, ji, bdev)) != cudaSuccess) return e;
@@ -1091,16 +1134,8 @@ static void reset_stats(rsn_ctx* c) {
   for (int k = 0; k < 2; ++k) c->ks_launches[k] = 0, c->ks_ms[k] = 0, c->ks_bytes[k] = 0;
 }
 
-extern "C" {
-
-rsn_status rsn_apply(rsn_ctx* c, int precision, int n_rhs, const double* E, const void* x_dev, void* y_dev) {
-  if (!c) return RSN_EINVAL;
-  rsn_status rs = commit_setup(c);
-  if (rs != RSN_OK) return rs;
-  if (n_rhs < 0 || (n_rhs > 0 && (!E || !x_dev || !y_dev))) RSN_FAIL(c, RSN_EINVAL, "bad arguments");
-  if (precision != RSN_FP64 && precision != RSN_MIXED) RSN_FAIL(c, RSN_EINVAL, "bad precision");
-  if (n_rhs == 0) return RSN_OK;
-  if ((rs = enter(c)) != RSN_OK) return rs;
+// y_k = A(E_k) x_k through the allocating per-call buffers of the context.
+static rsn_status apply_impl(rsn_ctx* c, int precision, int n_rhs, const double* E, const void* x_dev, void* y_dev) {
   const bool fp32 = precision == RSN_MIXED;
   CallBufs& q = c->cb;
   // small per-call arrays: E, junction ids, offsets, projections
@@ -1123,28 +1158,34 @@ rsn_status rsn_apply(rsn_ctx* c, int precision, int n_rhs, const double* E, cons
   b.voff = q.sys_xo.as<long long>();
   RSN_CUDA(c, cudaMemcpyAsync(c->bd.as<BatchDev>() + 1, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));
   const BatchDev* bdev = c->bd.as<BatchDev>() + 1;
+  // bulk-copy kernels need 16-byte aligned vectors; otherwise a register tiling
+  const bool aligned = (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0 && (reinterpret_cast<uintptr_t>(y_dev) % 16) == 0;
+  const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs, aligned);
   LaunchCfg cfg;
-  if ((rs = make_cfg(c, fp32, n_rhs, cfg)) != RSN_OK) return rs;
-  const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs);
+  rsn_status rs = make_cfg(c, t, choose_tiling(c, true, OP_RESID, n_rhs), cfg);
+  if (rs != RSN_OK) return rs;
   void* cbuf = q.out_t.p;
   if (c->n_proj > 0)
     RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->max_np, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
-  const bool aligned = (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0;
-  if (t.tma && aligned) {
-    RSN_CUDA(c, launch_op_tma(OP_APPLY, fp32, c->R, dim3(cfg.inner.n, n_rhs), t.threads, t.smem, c->st,
-                              cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
-  } else {
-    const Tiling t2 = [&] {
-      Tiling u = t;
-      u.tma = false;
-      u.smem = op_smem_bytes(fp32, OP_APPLY, c->R, u.TY, c->nx, c->n_proj);
-      u.threads = ((c->nx * u.TY + u.ppt - 1) / u.ppt + 31) / 32 * 32;
-      return u;
-    }();
-    RSN_CUDA(c, launch_op(OP_APPLY, fp32, c->R, t2.ppt, dim3(cfg.inner.n, n_rhs), t2.threads, t2.smem, c->st,
-                          cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
-  }
-  return leave(c);
+  RSN_CUDA(c, launch_inner(c, t, OP_APPLY, fp32, n_rhs, c->st, cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
+  return RSN_OK;
+}
+
+extern "C" {
+
+rsn_status rsn_apply(rsn_ctx* c, int precision, int n_rhs, const double* E, const void* x_dev, void* y_dev) {
+  if (!c) return RSN_EINVAL;
+  rsn_status rs = commit_setup(c);
+  if (rs != RSN_OK) return rs;
+  if (n_rhs < 0 || (n_rhs > 0 && (!E || !x_dev || !y_dev))) RSN_FAIL(c, RSN_EINVAL, "bad arguments");
+  if (n_rhs > kMaxApplyRhs) RSN_FAIL(c, RSN_EINVAL, "n_rhs = %d exceeds %d vectors per call; split the call", n_rhs, kMaxApplyRhs);
+  if (precision != RSN_FP64 && precision != RSN_MIXED) RSN_FAIL(c, RSN_EINVAL, "bad precision");
+  if (n_rhs == 0) return RSN_OK;
+  if ((rs = enter(c)) != RSN_OK) return rs;
+  rs = apply_impl(c, precision, n_rhs, E, x_dev, y_dev);
+  // the caller's stream is ordered after whatever was queued, also on failure
+  const rsn_status rl = leave(c);
+  return rs != RSN_OK ? rs : rl;
 }
 
 rsn_status rsn_solve_columns(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols,
@@ -1494,11 +1535,7 @@ static rsn_status bench_kernel_impl(rsn_ctx* c, int precision, int kind, int S, 
   LaunchCfg cfg;
   if ((rs = make_cfg(c, fp32, S, cfg)) != RSN_OK) return rs;
   auto launch = [&]() -> cudaError_t {
-    if (kind == 0)
-      return cfg.inner.tma ? launch_op_tma(OP_COCG, fp32, c->R, dim3(cfg.inner.n, S), cfg.inner.threads,
-                                           cfg.inner.smem, st, cfg.jt_inner, bdev, nullptr, nullptr, nullptr)
-                           : launch_op(OP_COCG, fp32, c->R, cfg.inner.ppt, dim3(cfg.inner.n, S), cfg.inner.threads,
-                                       cfg.inner.smem, st, cfg.jt_inner, bdev, nullptr, nullptr, nullptr);
+    if (kind == 0) return launch_inner(c, cfg.inner, OP_COCG, fp32, S, st, cfg.jt_inner, bdev, nullptr, nullptr, nullptr);
     if (kind == 1) return launch_cocg_update(fp32, S, c->jh.nB, st, cfg.jt_inner, bdev);
     return launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, dim3(cfg.resid.n, S), cfg.resid.threads, cfg.resid.smem,
                      st, cfg.jt_resid, bdev, nullptr, nullptr, nullptr);
@@ -1549,7 +1586,8 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
     const int lz = (c->nz + zt - 1) / zt;
     if (lz >= 2 * c->R + 2 || zt == 1) lzs.push_back(lz);
   }
-  for (int lz : lzs) cands.push_back({0, lz, 0, -1});
+  for (int lz : lzs) cands.push_back({0, lz, 0, 0});   // FP32 point-pair kernel where it applies
+  for (int lz : lzs) cands.push_back({0, lz, 0, -1});  // whole-plane bulk-copy kernel
   for (int p = 1; p <= 4; ++p)
     for (int ty : {c->ny, (c->ny + 1) / 2, (c->ny + 2) / 3})
       for (int lz : lzs) {
@@ -1590,7 +1628,7 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
   if (TY) *TY = bestc.TY;
   if (Lz) *Lz = bestc.Lz;
   if (ppt) *ppt = bestc.ppt;
-  if (tma) *tma = bestc.notma == -1 ? 1 : 0;
+  if (tma) *tma = bestc.notma == -1 ? 1 : (bestc.TY == 0 && bestc.ppt == 0 ? 2 : 0);
   if (best_gbs) *best_gbs = best;
   (void)fp32;
   return leave(c);
@@ -1643,6 +1681,35 @@ __global__ void noalloc_tables_kernel(int n, long long N, long long* voff, int* 
   }
 }
 
+// The work of one allocation-free call, between enter() and leave().
+static rsn_status apply_noalloc_impl(rsn_ctx* c, int precision, int n_rhs, const double* E, const void* x_dev,
+                                     void* y_dev, unsigned char* base, size_t o_E, size_t o_voff, size_t o_junc,
+                                     size_t o_c) {
+  const bool fp32 = precision == RSN_MIXED;
+  BatchDev b;
+  memset(&b, 0, sizeof(b));
+  b.nslots = n_rhs;
+  b.E = reinterpret_cast<double*>(base + o_E);
+  b.voff = reinterpret_cast<long long*>(base + o_voff);
+  b.junc = reinterpret_cast<int*>(base + o_junc);
+  void* cbuf = base + o_c;
+  const BatchDev* bdev = reinterpret_cast<const BatchDev*>(base);
+  RSN_CUDA(c, cudaMemcpyAsync(base, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));
+  RSN_CUDA(c, cudaMemcpyAsync(b.E, E, n_rhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  noalloc_tables_kernel<<<(n_rhs + 255) / 256, 256, 0, c->st>>>(n_rhs, c->N, b.voff, b.junc);
+  RSN_CUDA(c, cudaGetLastError());
+  // bulk-copy kernels need 16-byte aligned vectors; otherwise a register tiling
+  const bool aligned = (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0 && (reinterpret_cast<uintptr_t>(y_dev) % 16) == 0;
+  const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs, aligned);
+  LaunchCfg cfg;
+  rsn_status rs = make_cfg(c, t, choose_tiling(c, true, OP_RESID, n_rhs), cfg);
+  if (rs != RSN_OK) return rs;
+  if (c->n_proj > 0)
+    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->max_np, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
+  RSN_CUDA(c, launch_inner(c, t, OP_APPLY, fp32, n_rhs, c->st, cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
+  return RSN_OK;
+}
+
 extern "C" rsn_status rsn_apply_noalloc(rsn_ctx* c, int precision, int n_rhs, const double* E, const void* x_dev,
                                         void* y_dev) {
   static std::mutex mu;
@@ -1667,47 +1734,26 @@ extern "C" rsn_status rsn_apply_noalloc(rsn_ctx* c, int precision, int n_rhs, co
              "rsn_apply_noalloc: %d vectors with %d projectors need %zu bytes of scratch, more than the %zu-byte "
              "fixed array; split the call",
              n_rhs, c->n_proj, need, kNoAllocScratchBytes);
+  if (n_rhs > kMaxApplyRhs)
+    RSN_FAIL(c, RSN_EINVAL, "rsn_apply_noalloc: n_rhs = %d exceeds %d vectors per call; split the call", n_rhs,
+             kMaxApplyRhs);
   if (c->device < 0 || c->device >= kNoAllocMaxDevices) RSN_FAIL(c, RSN_EINVAL, "device index too large");
   rsn_status rs = enter(c);  // makes the context's device current
   if (rs != RSN_OK) return rs;
-  unsigned char* base;
+  unsigned char* base = nullptr;
   {
     // first call on a device: host code needs the device address of the array
     std::lock_guard<std::mutex> lock(mu);
     if (!scratch_addr[c->device]) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) RSN_FAIL(c, RSN_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      scratch_addr[c->device] = p;
+      if (e == cudaSuccess) scratch_addr[c->device] = p;
+      else c->err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
     }
     base = static_cast<unsigned char*>(scratch_addr[c->device]);
   }
-  const bool fp32 = precision == RSN_MIXED;
-  BatchDev b;
-  memset(&b, 0, sizeof(b));
-  b.nslots = n_rhs;
-  b.E = reinterpret_cast<double*>(base + o_E);
-  b.voff = reinterpret_cast<long long*>(base + o_voff);
-  b.junc = reinterpret_cast<int*>(base + o_junc);
-  void* cbuf = base + o_c;
-  const BatchDev* bdev = reinterpret_cast<const BatchDev*>(base);
-  RSN_CUDA(c, cudaMemcpyAsync(base, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));
-  RSN_CUDA(c, cudaMemcpyAsync(b.E, E, n_rhs * sizeof(double), cudaMemcpyHostToDevice, c->st));
-  noalloc_tables_kernel<<<(n_rhs + 255) / 256, 256, 0, c->st>>>(n_rhs, c->N, b.voff, b.junc);
-  RSN_CUDA(c, cudaGetLastError());
-  LaunchCfg cfg;
-  if ((rs = make_cfg(c, fp32, n_rhs, cfg)) != RSN_OK) return rs;
-  const Tiling t = choose_tiling(c, !fp32, OP_APPLY, n_rhs);
-  if (c->n_proj > 0)
-    RSN_CUDA(c, launch_project(2, fp32, n_rhs, c->n_groups, c->max_np, c->st, cfg.jt_inner, bdev, x_dev, cbuf));
-  if (t.tma && (reinterpret_cast<uintptr_t>(x_dev) % 16) == 0) {
-    RSN_CUDA(c, launch_op_tma(OP_APPLY, fp32, c->R, dim3(cfg.inner.n, n_rhs), t.threads, t.smem, c->st,
-                              cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
-  } else {
-    const size_t smem = op_smem_bytes(fp32, OP_APPLY, c->R, t.TY, c->nx, c->n_proj);
-    const int threads = ((c->nx * t.TY + t.ppt - 1) / t.ppt + 31) / 32 * 32;
-    RSN_CUDA(c, launch_op(OP_APPLY, fp32, c->R, t.ppt, dim3(cfg.inner.n, n_rhs), threads, smem, c->st,
-                          cfg.jt_inner, bdev, x_dev, y_dev, cbuf));
-  }
-  return leave(c);
+  rs = base ? apply_noalloc_impl(c, precision, n_rhs, E, x_dev, y_dev, base, o_E, o_voff, o_junc, o_c) : RSN_ECUDA;
+  // the caller's stream is ordered after whatever was queued, also on failure
+  const rsn_status rl = leave(c);
+  return rs != RSN_OK ? rs : rl;
 }

@@ -23,6 +23,7 @@ constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
 // by the zero-padded tail of an atom's last value quad
 constexpr int kCePad = 16;
 constexpr int kMaxGraphIters = 256;
+constexpr int kMaxApplyRhs = 65535;  // vectors per operator-application call (grid y dimension)
 constexpr int kSchedThreads = 1024;
 // CTA rows of the kernels that work only on NEW / CHECK slots (zero, true
 // residual and its projections, x update): each row takes list entries
@@ -169,6 +170,16 @@ size_t op_smem_bytes(bool fp32, int mode, int R, int TY, int nx, int n_proj);
 cudaError_t launch_op_tma(int mode, bool fp32, int R, dim3 grid, int threads, size_t smem, cudaStream_t st,
                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out, const void* c_in);
 size_t op_tma_smem_bytes(bool fp32, int mode, int R, int nx, int ny, int n_proj);
+// FP32 point-pair operator kernel with plane streaming (OP_COCG / OP_APPLY):
+// whole planes, nx even, 16-byte aligned vectors; big: the one-CTA-per-SM
+// variant for planes of more than 2 * kPairThreads points
+constexpr int kPairThreads = 288;     // threads per CTA of the two-CTAs-per-SM variant
+constexpr int kPairThreadsBig = 640;  // one CTA per SM (planes of up to 1280 points)
+constexpr int kPairStages = 4;        // input planes in flight per CTA
+constexpr int kPairXO = 8;            // zero columns left of x = 0 in the exchange tile (>= R, even)
+cudaError_t launch_op_pair(int mode, int R, bool big, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out, const void* c_in);
+size_t op_pair_smem_bytes(int mode, int R, int nx, int ny, int n_proj);
 
 cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,

@@ -705,7 +705,9 @@ __global__ void __launch_bounds__(256) grad_sys_kernel(int nsys, long long N, co
   cudaError_t launch_op_R##R(int, bool, int, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev*, \
                              const void*, void*, const void*);                                                 \
   cudaError_t launch_op_tma_R##R(int, bool, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev*,  \
-                                 const void*, void*, const void*);
+                                 const void*, void*, const void*);                                             \
+  cudaError_t launch_op_pair_R##R(int, bool, dim3, int, size_t, cudaStream_t, const JuncDev*, const BatchDev*, \
+                                  const void*, void*, const void*);
 RSN_DECL_OP(1)
 RSN_DECL_OP(2)
 RSN_DECL_OP(3)
@@ -738,6 +740,27 @@ cudaError_t launch_op_tma(int mode, bool fp32, int R, dim3 grid, int threads, si
     case 6: return launch_op_tma_R6(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_op_pair(int mode, int R, bool big, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out, const void* c_in) {
+  switch (R) {
+    case 1: return launch_op_pair_R1(mode, big, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 2: return launch_op_pair_R2(mode, big, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 3: return launch_op_pair_R3(mode, big, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 4: return launch_op_pair_R4(mode, big, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 5: return launch_op_pair_R5(mode, big, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    case 6: return launch_op_pair_R6(mode, big, grid, threads, smem, st, jt, b, x_in, y_out, c_in);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t op_pair_smem_bytes(int mode, int R, int nx, int ny, int n_proj) {
+  const size_t nin = mode == OP_COCG ? 2 : 1;
+  const size_t pitch = (size_t)nx + 2 * kPairXO;
+  const size_t cep = mode == OP_APPLY ? (size_t)n_proj + kCePad : 0;
+  return sizeof(float2) * (kPairStages * nin * (size_t)nx * ny + 2 * (size_t)(ny + 2 * R) * pitch + cep) + 16 +
+         8 * kPairStages;
 }
 
 size_t op_tma_smem_bytes(bool fp32, int mode, int R, int nx, int ny, int n_proj) {

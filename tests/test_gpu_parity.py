@@ -35,6 +35,11 @@ JUNCTIONS = {
     "spd_R6": lambda: P.molecular_junction(seed=4, nx=12, ny=12, nz=40, fd_half_order=6, n_wells=3, lmax=2,
                                            n_cap=6, h=0.3),
     "wide_R2": lambda: P.molecular_junction(seed=6, nx=40, ny=36, nz=20, fd_half_order=2, n_wells=2, n_cap=3),
+    # the benchmark's cross-section (plane streaming above 48 KiB of shared memory)
+    "bench_plane_R4": lambda: P.molecular_junction(seed=7, nx=24, ny=24, nz=30, n_wells=3, n_cap=4),
+    "r5": lambda: P.molecular_junction(seed=9, nx=14, ny=14, nz=36, fd_half_order=5, n_wells=3, n_cap=4),
+    # one-CTA-per-SM point-pair variant (planes of more than 576 points)
+    "big_plane_R4": lambda: P.molecular_junction(seed=10, nx=32, ny=30, nz=24, n_wells=3, n_cap=4),
 }
 
 
