@@ -4,11 +4,23 @@
 Workload (one "step"): the 24x24x120 synthetic molecular junction (69,120
 points, h = 0.35 bohr, 8th-order FD, soft-square leads, 20 Gaussian wells, 20
 atoms x 4 s/p KB projectors, 8-plane quadratic CAP, seed 1) at one energy from
-128 in [0.16, 0.24] Ha: the partial T(E) and dT(E)/dV_loc over a batch of
-288 right-CAP columns (every 16th of the 4,608) = 288 forward + 288
-adjoint COCG solves, FP32 Krylov recurrence with FP64 reliable updates to a
-true relative residual of 1e-10, FP64 T and gradient sums.  Every solve
-counts as one unit of the metric.
+128 in [0.16, 0.24] Ha: the partial T(E) and dT(E)/dV_loc over a batch of 288
+right-CAP columns (every 16th of the 4,608).  Each column is one unit of the
+metric and costs two solves: its forward COCG solve x_j = G e_j and its
+adjoint solve lambda_j = G (Gamma_L o conj x_j).  FP32 Krylov recurrence with
+FP64 reliable updates to a true relative residual of 1e-10, FP64 T and
+gradient sums.
+
+Beside the timed steps the JSON line carries
+  * ``roofline``: the COCG operator kernel timed with CUDA events in a separate
+    pass over the same energies (no events inside the timed region);
+  * ``forward_T``: T(E) alone over all 4,608 right-CAP columns at two seeded
+    energies, mixed precision and FP64 on the same columns, with |dT| per energy;
+  * ``parity``: T and per-column contributions of 16 golden columns at three
+    energies against the oracle's sparse-LU values (tests/golden);
+  * ``e2e``: the step through the public API from host buffers (potential in,
+    T and dV out) over the timed steps' energies;
+  * ``cpu_baseline``: the oracle on columns and energies of the timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,16 +48,18 @@ UNIT = "solves/s"
 N_ENERGIES = 128
 E_LO, E_HI = 0.16, 0.24
 WORKLOAD = ("junction 24x24x120 (N=69,120), h=0.35, 8th-order FD, 20 atoms x 4 KB projectors, "
-            "8-plane quadratic CAP, seed 1; mixed precision (complex FP32 COCG + FP64 refinement to 1e-10)")
+            "8-plane quadratic CAP, seed 1; mixed precision (complex FP32 COCG + FP64 refinement to 1e-10); "
+            "one unit = one right-CAP column with its forward and adjoint solve")
 CPU_SAMPLE_RTOL = 1e-10
-
-
+GOLDEN = os.path.join(ROOT, "tests", "golden", "junction_24x24x120_tc.txt")
 
 # DRAM bytes per algorithmic byte of the COCG operator kernel, from one ncu
-# capture (python -m paper_1401_0782_gb300.kernel_bench --kind op --slots 256
-# --reps 3; dram__bytes_read.sum + dram__bytes_write.sum = 557.6 MB against
-# 566.2 MB algorithmic).  Taken again whenever that kernel changes.
-OP_DRAM_PER_ALG_BYTE = 557.584128 / 566.23104
+# capture of the kernel micro-benchmark (python -m paper_1401_0782_gb300.kernel_bench
+# --kind op --slots 256 --reps 3): dram__bytes_read.sum + dram__bytes_write.sum
+# over 32 B x 69,120 points x 256 systems.  None until that capture is taken
+# for the current kernel.
+OP_DRAM_PER_ALG_BYTE = None
+
 
 def _env_int(k, d):
     try:
@@ -172,36 +186,43 @@ def energy_for(rank: int, world: int, k: int) -> float:
 # CPU oracle leg (bounded sample; spawn pool, never forked after CUDA init)
 # ---------------------------------------------------------------------------
 def _oracle_worker(args):
+    """Forward + adjoint solve of one column by the oracle's Krylov route."""
     col, E, rtol = args
     sys.path.insert(0, ROOT)
     import oracle as O
     from paper_1401_0782_gb300 import problems as P
+    import numpy as np
     j = P.molecular_junction(seed=1)
     t0 = time.perf_counter()
-    O.solve_columns(j, E, [col], method="krylov", rtol=rtol)
+    # the steps of the oracle's transmission_grad at the bench tolerance:
+    # forward column, then the adjoint with the same operator
+    X, solver = O.solve_columns(j, E, [col], return_lu=True, method="krylov", rtol=rtol)
+    solver.solve(j.gamma_l[:, None] * np.conj(X))
     return time.perf_counter() - t0
 
 
-def oracle_sample(n_solves: int, cores: int, E: float = 0.2):
-    """Run n_solves oracle column solves of the bench junction over `cores`
-    spawn processes; returns (solves/s, wall seconds)."""
+def oracle_sample(pairs, cores: int):
+    """Forward + adjoint oracle solves of the (column, energy) pairs over `cores`
+    spawn processes; returns (columns/s, wall seconds)."""
     import multiprocessing as mp
-    from paper_1401_0782_gb300 import problems as P
-    import numpy as np
-    j = P.molecular_junction(seed=1)
-    cols = j.right_columns()
-    rng = np.random.default_rng(8)
-    pick = rng.choice(cols, n_solves, replace=False)
     ctx = mp.get_context("spawn")
     # one thread per worker process: the pool, not BLAS, uses the cores
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_worker, [(int(cols[0]), E, 1e-2)] * cores)  # import + setup warm-up, not timed
+        pool.map(_oracle_worker, [(pairs[0][0], pairs[0][1], 1e-2)] * cores)  # import + setup warm-up, not timed
         t0 = time.perf_counter()
-        pool.map(_oracle_worker, [(int(c), E, CPU_SAMPLE_RTOL) for c in pick])
+        pool.map(_oracle_worker, [(c, E, CPU_SAMPLE_RTOL) for c, E in pairs])
         wall = time.perf_counter() - t0
-    return n_solves / wall, wall
+    return len(pairs) / wall, wall
+
+
+def sample_pairs(cols, energies, n):
+    """n (column, energy) pairs: columns of the step's set, cycling over the energies."""
+    import numpy as np
+    rng = np.random.default_rng(8)
+    pick = rng.choice(cols, n, replace=False)
+    return [(int(c), float(energies[i % len(energies)])) for i, c in enumerate(pick)]
 
 
 def cpu_cores():
@@ -211,9 +232,42 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def load_golden():
+    """{energy index: (E, cols, t_c)} from the oracle-written golden file, or None."""
+    import numpy as np
+    if not os.path.exists(GOLDEN):
+        return None
+    rows = [ln.split() for ln in open(GOLDEN) if ln.strip() and not ln.startswith("#")]
+    out = {}
+    for k, E, c, t, _ in rows:
+        out.setdefault(int(k), (float(E), [], []))
+        out[int(k)][1].append(int(c))
+        out[int(k)][2].append(float(t))
+    return {k: (E, np.array(c, np.int32), np.array(t)) for k, (E, c, t) in out.items()}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def passes_per_iteration(j):
+    """Algorithmic vector passes (one complex vector of N points read or written
+    once) per COCG iteration of one system, by kernel."""
+    import numpy as np
+    cnt = np.zeros(j.N, np.int64)
+    atoms = {}
+    for p in range(j.n_proj):
+        idx = j.proj_idx[j.proj_offsets[p]:j.proj_offsets[p + 1]]
+        atoms.setdefault(idx.tobytes(), idx)
+    for idx in atoms.values():
+        cnt[idx] += 1
+    sup = float(np.count_nonzero(cnt)) / j.N
+    gath = float(cnt.sum()) / j.N
+    d = {"operator": 4.0, "update": 6.0, "projector_term": 2.0 * sup, "r_projection": gath}
+    d["total"] = sum(d.values())
+    d["floor"] = 6.0
+    return d
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -224,26 +278,26 @@ def run_ours(args):
     dist, rank, local, world = dist_init()
     torch.cuda.set_device(local)
     j = P.molecular_junction(seed=1)
-    cols = j.right_columns()
+    all_cols = j.right_columns()
+    cols = all_cols
     if args.cols_per_step and args.cols_per_step < cols.size:
         cols = cols[:: int(np.ceil(cols.size / args.cols_per_step))]
     n_cols = int(cols.size)
-    solves_per_step = 2 * n_cols
     ctx = B.Context(local).set_junction(j)
-    opts = B.default_opts(B.RSN_MIXED, timing=1, deadline_ms=args.deadline * 1e3)
+    opts = B.default_opts(B.RSN_MIXED, deadline_ms=args.deadline * 1e3)
     # operator-kernel tile for this grid and slot count (untimed set-up)
-    tuned = ctx.autotune(B.RSN_MIXED, min(2048, max(256, solves_per_step // 4)))
+    tuned = ctx.autotune(B.RSN_MIXED, min(2048, max(256, 2 * n_cols // 4)))
     print(f"[bench] autotuned tile {tuned}", file=sys.stderr, flush=True)
     dV = torch.empty(j.N, dtype=torch.float64, device=f"cuda:{local}")
 
-    def step(k):
+    def step(k, o):
         E = energy_for(rank, world, k)
-        T, _ = ctx.transmission_vjp([E], [1.0], cols, opts, dV_out=dV)
+        T, _ = ctx.transmission_vjp([E], [1.0], cols, o, dV_out=dV)
         return T
 
     t_w = time.perf_counter()
     for k in range(args.warmup):
-        step(k)
+        step(k, opts)
         print(f"[bench] warm-up step {k}: {time.perf_counter() - t_w:.1f} s {ctx.last_stats()}", file=sys.stderr,
               flush=True)
     torch.cuda.synchronize()
@@ -256,52 +310,59 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev0.record(stream)
     t_wall = time.perf_counter()
+    launches = iters = fallbacks = 0
+    step_stats = []
+    timed = list(range(args.warmup, args.warmup + args.steps))
+    for k in timed:
+        step(k, opts)
+        st = ctx.last_stats()
+        launches += st["launches"]
+        iters += st["krylov_iters"]
+        fallbacks += st["fp64_fallbacks"]
+        step_stats.append((k, st))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks.stop()
+    for k, st in step_stats:
+        print(f"[bench] step {k} E={energy_for(rank, world, k):.5f}: {st}", file=sys.stderr, flush=True)
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(dist, ms)
+    total_units = sum_over_ranks(dist, float(args.steps * n_cols))
+    value = total_units / (ms_max / 1e3)
+
+    # ---- roofline: the operator kernel timed with events in its own pass -----
+    ot = B.default_opts(B.RSN_MIXED, deadline_ms=args.deadline * 1e3, timing=1)
     kb = kms = 0.0
     klaunch = 0
     ub = ums = 0.0
-    launches = 0
-    iters = 0
-    fallbacks = 0
-    for k in range(args.warmup, args.warmup + args.steps):
-        step(k)
-        s0, s1, st = ctx.kernel_stats(0), ctx.kernel_stats(1), ctx.last_stats()
+    for k in timed[: max(1, min(len(timed), args.roofline_steps))]:
+        step(k, ot)
+        s0, s1 = ctx.kernel_stats(0), ctx.kernel_stats(1)
         kb += s0["bytes"]
         kms += s0["ms"]
         klaunch += s0["launches"]
         ub += s1["bytes"]
         ums += s1["ms"]
-        launches += st["launches"]
-        print(f"[bench] step {k}: {st} op {s0['ms']:.0f} ms / {s0['launches']}", file=sys.stderr, flush=True)
-        iters += st["krylov_iters"]
-        fallbacks += st["fp64_fallbacks"]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
-    clocks.stop()
-    if dist is not None:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    ms_max = max_over_ranks(dist, ms)
-    total_solves = sum_over_ranks(dist, float(args.steps * solves_per_step))
-    value = total_solves / (ms_max / 1e3)
 
     # ---- end to end through the public API with host buffers -------------
-    e2e_steps = max(1, min(2, args.steps))
-    h2d = d2h = 0
+    # every step uploads its potential (host -> device, the input of T and
+    # dT/dV_loc) and reads T and dV back; energies of the timed steps
+    e2e_ks = [timed[i % len(timed)] for i in range(max(5, len(timed)))]
+    v_host = np.ascontiguousarray(j.v_loc, dtype=np.float64)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     te = time.perf_counter()
-    for k in range(e2e_steps):
-        E = energy_for(rank, world, k)
-        ctx_e = B.Context(local)
-        ctx_e.set_junction(j)  # host -> device copy of the setup arrays
-        T_h, dV_h = ctx_e.transmission_vjp([E], [1.0], cols, opts)  # host T, host dV (device -> host)
-        ctx_e.close()
-        h2d = j.nbytes_setup() + 8 + 8 + 4 * n_cols
-        d2h = dV_h.nbytes + T_h.nbytes
+    for k in e2e_ks:
+        ctx.set_potential(v_host)
+        T_h, dV_h = ctx.transmission_vjp([energy_for(rank, world, k)], [1.0], cols, opts)
     e2e_s = max_over_ranks(dist, time.perf_counter() - te)
-    e2e_value = sum_over_ranks(dist, float(e2e_steps * solves_per_step)) / e2e_s
+    e2e_value = sum_over_ranks(dist, float(len(e2e_ks) * n_cols)) / e2e_s
+    h2d = v_host.nbytes + 8 + 8 + cols.nbytes
+    d2h = dV_h.nbytes + T_h.nbytes
 
     result = None
     if rank == 0:
@@ -314,72 +375,118 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
             "config": {
                 "workload": WORKLOAD, "grid": [j.nx, j.ny, j.nz], "N": j.N, "fd_order": 2 * j.fd_half_order,
-                "n_proj": j.n_proj, "columns_per_step": n_cols, "solves_per_step": solves_per_step,
-                "step": "partial T(E) + dT/dV_loc at one energy over every 16th right-CAP column: "
-                        "forward + adjoint COCG solve per column",
+                "n_proj": j.n_proj, "columns_per_step": n_cols, "solves_per_step": 2 * n_cols,
+                "unit_definition": "one right-CAP column j: forward solve x_j = G e_j and adjoint solve "
+                                   "lambda_j = G (Gamma_L o conj x_j), both to true relative residual 1e-10",
+                "step": "partial T(E) + dT/dV_loc at one energy over every 16th right-CAP column",
                 "energies": f"step k on rank r: E[37 (r + k*world) mod {N_ENERGIES}] of linspace({E_LO},{E_HI},{N_ENERGIES})",
                 "tol": opts.tol, "tol_inner": opts.tol_inner,
                 "l2": "inputs larger than L2: per-step working set "
-                      f"{(j.N * n_cols * (16 + 16 + 5 * 8)) / 1e9:.1f} GB",
+                      f"{(j.N * 2 * n_cols * (16 + 16 + 5 * 8)) / 1e9:.1f} GB",
                 "parallelism": f"replicas x{world}: energies sharded over ranks, no collective in the data path",
                 "tile": tuned,
             },
             "roofline": {
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": (OP_DRAM_PER_ALG_BYTE * kb / klaunch) if klaunch else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch with 256 active "
-                                  "slots (0.985 of its algorithmic bytes), scaled to this run's mean launch",
-                "kernel": "op_kernel<float,4,*,OP_COCG> (fused p-update + 25-point stencil + V/CAP + p^T A p; "
-                          "the projector term of A p is added by the support-point kernel)",
+                "traffic": (OP_DRAM_PER_ALG_BYTE * kb / klaunch) if (klaunch and OP_DRAM_PER_ALG_BYTE) else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per algorithmic byte of one "
+                                  "kernel_bench launch (256 slots), scaled to this run's mean launch",
+                "kernel": "op_pair_kernel<4,OP_COCG> (p = r + beta p_old, 25-point stencil + V/CAP on point "
+                          "pairs with bulk-copied planes, p^T A p); the projector term of A p is added on the "
+                          "support points by the update side",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
                                "fallback 6.8 TB/s",
                 "algorithmic_bytes": "32 B per active system per grid point (read r, p_old; write p_new, q)",
-                "launches_timed": klaunch, "kernel_ms": kms,
+                "timing": f"CUDA events around every operator launch on the library stream, in a separate pass "
+                          f"over the first {max(1, min(len(timed), args.roofline_steps))} timed steps' energies",
+                "launches_timed": klaunch, "kernel_ms": kms, "mean_launch_bytes": kb / klaunch if klaunch else None,
                 "update_kernel_gbs": upd,
-                "update_kernel_note": "projector-term kernel on the support points + COCG update, "
-                                      "6 vectors x 8 B per point algorithmic",
+                "update_kernel_note": "support-point projector term + COCG update, 6 vectors x 8 B per point algorithmic",
             },
+            "passes_per_iteration": passes_per_iteration(j),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "steps": e2e_steps},
+                    "steps": len(e2e_ks), "energies": "those of the timed steps",
+                    "per_step": "set_potential (host V_loc) + transmission_vjp with host T and dV"},
             "gpu_launches": int(launches),
-            "krylov_iters_per_solve": iters / float(args.steps * solves_per_step),
+            "krylov_iters_per_solve": iters / float(args.steps * 2 * n_cols),
             "fp64_fallback_solves": int(fallbacks),
             "clocks": clocks.summary(),
             "wall_s": wall,
         }
-    # ---- FP64 comparison on a column subset (same energy, same columns) ----
+
+    # ---- forward T over every right-CAP column: mixed against FP64 ----------
     if rank == 0 and not args.no_fp64:
-        sub = cols[:: max(1, n_cols // args.fp64_cols)]
-        E0 = 0.2
-        o64 = B.default_opts(B.RSN_FP64)
-        om = B.default_opts(B.RSN_MIXED)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        T64, _ = ctx.transmission_vjp([E0], [1.0], sub, o64, dV_out=dV)
-        t64 = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        Tm, _ = ctx.transmission_vjp([E0], [1.0], sub, om, dV_out=dV)
-        tm = time.perf_counter() - t0
-        result["fp64"] = {
-            "sample": f"E=0.2 Ha, {sub.size} columns (forward + adjoint)",
-            "fp64_solves_per_s": 2 * sub.size / t64, "mixed_solves_per_s": 2 * sub.size / tm,
-            "mixed_over_fp64": t64 / tm, "T_fp64": float(T64[0]), "T_mixed": float(Tm[0]),
-            "abs_dT_mixed_vs_fp64": float(abs(Tm[0] - T64[0])),
+        rng = np.random.default_rng(17)
+        E_grid = np.linspace(E_LO, E_HI, N_ENERGIES)
+        eidx = sorted(rng.choice(N_ENERGIES, args.fwd_energies, replace=False).tolist())
+        fcols = all_cols[:: max(1, all_cols.size // args.fwd_cols)] if args.fwd_cols else all_cols
+        per_e = []
+        tm_tot = t64_tot = 0.0
+        for i in eidx:
+            E = float(E_grid[i])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Tm = ctx.transmission([E], fcols, B.default_opts(B.RSN_MIXED))[0]
+            tm = time.perf_counter() - t0
+            sm = ctx.last_stats()
+            t0 = time.perf_counter()
+            T64 = ctx.transmission([E], fcols, B.default_opts(B.RSN_FP64))[0]
+            t64 = time.perf_counter() - t0
+            s64 = ctx.last_stats()
+            tm_tot += tm
+            t64_tot += t64
+            per_e.append({"E": E, "T_mixed": float(Tm), "T_fp64": float(T64), "abs_dT": float(abs(Tm - T64)),
+                          "rel_dT": float(abs(Tm - T64) / abs(T64)) if T64 else None,
+                          "mixed_s": tm, "fp64_s": t64,
+                          "iters_per_solve_mixed": sm["krylov_iters"] / fcols.size,
+                          "iters_per_solve_fp64": s64["krylov_iters"] / fcols.size,
+                          "fp64_fallbacks": sm["fp64_fallbacks"]})
+        n = fcols.size * len(eidx)
+        result["forward_T"] = {
+            "sample": f"{fcols.size} right-CAP columns x energies {eidx} of linspace({E_LO},{E_HI},{N_ENERGIES}); "
+                      "forward solves only, host-timed library calls",
+            "mixed_solves_per_s": n / tm_tot, "fp64_solves_per_s": n / t64_tot,
+            "mixed_over_fp64": t64_tot / tm_tot, "per_energy": per_e,
+            "note": "T ~ 1e-19..1e-13 in this window (every lead channel is closed), so |dT| <= 1e-6 is met by "
+                    "construction; rel_dT is the meaningful figure",
         }
+
+    # ---- parity against the oracle's golden columns ------------------------
+    if rank == 0 and not args.no_fp64:
+        gold = load_golden()
+        if gold:
+            rows = []
+            for k, (E, gc, tg) in sorted(gold.items()):
+                Tg = 4.0 * float(np.sum(j.gamma_r[gc] * tg))
+                row = {"energy_index": k, "E": E, "T_oracle": Tg}
+                for name, prec in (("fp64", B.RSN_FP64), ("mixed", B.RSN_MIXED)):
+                    x, _, _ = ctx.solve_columns([E], gc, B.default_opts(prec))
+                    xv = x[0]
+                    gl = torch.tensor(j.gamma_l, device=xv.device)
+                    tc = (gl[None, :] * (xv.real ** 2 + xv.imag ** 2)).sum(1).cpu().numpy()
+                    T = float(ctx.transmission([E], gc, B.default_opts(prec))[0])
+                    row[f"T_{name}"] = T
+                    row[f"rel_dT_{name}"] = abs(T - Tg) / abs(Tg)
+                    row[f"max_rel_dt_col_{name}"] = float(np.max(np.abs(tc - tg) / np.abs(tg)))
+                rows.append(row)
+            result["parity"] = {"golden": os.path.relpath(GOLDEN, ROOT), "columns": int(next(iter(gold.values()))[1].size),
+                                "per_energy": rows}
     ctx.close()
 
     # ---- CPU oracle baseline (rank 0 at N = 1 only) ------------------------
     if rank == 0:
         if world == 1 and not args.no_cpu:
             cores = min(cpu_cores(), 16)
-            v, wall_cpu = oracle_sample(2 * cores, cores)
+            Es = [energy_for(rank, world, k) for k in timed[:2]]
+            pairs = sample_pairs(cols, Es, cores)
+            v, wall_cpu = oracle_sample(pairs, cores)
             result["cpu_baseline"] = {
                 "value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": f"{2 * cores} forward column solves of the bench junction at E=0.2 Ha, two per core, "
-                          f"by the oracle's Krylov route to relative residual {CPU_SAMPLE_RTOL:g} (complex128, "
-                          f"certified by its true residual; its LU route takes minutes per energy at this size); "
-                          f"wall {wall_cpu:.1f} s",
+                "sample": f"{len(pairs)} columns of the step's column set at the first two timed energies "
+                          f"({', '.join(f'{e:.5f}' for e in Es)} Ha), one per core, each a forward and an adjoint "
+                          f"solve by the oracle's Krylov route (complex128, certified true residual) to relative "
+                          f"residual {CPU_SAMPLE_RTOL:g}; wall {wall_cpu:.1f} s",
             }
         print(json.dumps(result), flush=True)
     if dist is not None:
@@ -394,18 +501,24 @@ def run_reference(args):
     world = _env_int("WORLD_SIZE", 1)
     if rank != 0:
         return
+    import numpy as np
+    from paper_1401_0782_gb300 import problems as P
+    j = P.molecular_junction(seed=1)
+    cols = j.right_columns()
+    if args.cols_per_step and args.cols_per_step < cols.size:
+        cols = cols[:: int(np.ceil(cols.size / args.cols_per_step))]
     cores = min(cpu_cores(), 16)
-    for _ in range(args.warmup):
-        oracle_sample(cores, cores)
     times = []
-    for _ in range(args.steps):
-        v, wall = oracle_sample(cores, cores)
-        times.append(wall)
+    for k in range(args.warmup + args.steps):
+        pairs = sample_pairs(cols, [energy_for(0, 1, k)], cores)
+        v, wall = oracle_sample(pairs, cores)
+        if k >= args.warmup:
+            times.append(wall)
     total = args.steps * cores
     value = total / sum(times)
-    sample = (f"{cores} forward column solves of the bench junction per step at E=0.2 Ha, one per core, "
-              f"by the oracle's Krylov route (complex128, certified true residual) to relative residual "
-              f"{CPU_SAMPLE_RTOL:g}")
+    sample = (f"{cores} columns of the bench step's column set per step at that step's energy, one per core, "
+              f"each a forward and an adjoint solve by the oracle's Krylov route (complex128, certified true "
+              f"residual) to relative residual {CPU_SAMPLE_RTOL:g}")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
@@ -421,13 +534,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cols-per-step", type=int, default=288,
                     help="columns per step: every k-th of the 4,608 right-CAP columns (0 = all)")
-    ap.add_argument("--fp64-cols", type=int, default=96, help="columns in the FP64 comparison sample")
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--roofline-steps", type=int, default=2, help="steps of the event-timed roofline pass")
+    ap.add_argument("--fwd-energies", type=int, default=2, help="energies of the forward-T comparison")
+    ap.add_argument("--fwd-cols", type=int, default=0, help="columns of the forward-T comparison (0 = all 4,608)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the forward-T and parity legs")
     ap.add_argument("--deadline", type=float, default=240.0, help="seconds allowed per library call")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

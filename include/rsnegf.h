@@ -87,11 +87,21 @@ typedef struct {
                            column, and on large, nearly resonant junctions the FP64 recurrence
                            of an adjoint can level off above a tol that its forward column
                            meets; a looser target here keeps tol for the columns and T */
+    double tol_T;       /* goal-oriented finish of the forward columns (b = e_j): once the
+                           true residual meets tol, iterations continue until
+                           t_j = sum_{i in L} Gamma_L,i |x_j(i)|^2 -- the column's share of
+                           Eq. T-realspace -- changes by at most tol_T * t_j between two true
+                           residuals.  Where every lead channel is closed, x_j is exponentially
+                           small on the Gamma_L support and a residual of tol relative to the
+                           whole column fixes t_j only to ~1e-4 (tol 1e-10) or ~1e-7 (1e-13);
+                           the iterate keeps converging there after its residual reaches the
+                           rounding floor.  0 = residual criterion alone. */
 } rsn_solver_opts;
 
-/* Defaults for a precision: FP64 -> tol 1e-13, tol_inner 1e-6, max_iter 20000;
-   MIXED -> tol 1e-10, tol_inner 1e-1, max_iter 3000 (a system that needs more,
-   or whose FP32 recurrence stalls, is solved again in FP64 from zero);
+/* Defaults for a precision: FP64 -> tol 1e-13, tol_T 1e-10, tol_inner 1e-6,
+   max_iter 20000; MIXED -> tol 1e-10, tol_T 1e-7, tol_inner 1e-1, max_iter 3000
+   (a system that needs more, or whose FP32 recurrence stalls, is solved again
+   in FP64 from zero);
    both: tol_adjoint 0 (= tol), max_outer 64, graphs on (16 iterations per
    replay), timing off. */
 void rsn_default_opts(int precision, rsn_solver_opts* opts);
@@ -174,6 +184,58 @@ rsn_status rsn_solve_columns(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
 rsn_status rsn_transmission(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
                             const int32_t* cols, const rsn_solver_opts* opts, double* T);
 
+/* Shifted COCG over an energy window: columns x_{e,c} = G^r(E[e]) e_{cols[c]}
+   for every energy from ONE Krylov space per column.  A(E) = E 1 - H_op, so
+   A(E[e]) = A(E_s) + (E[e] - E_s) 1 (Eq. G: the energy enters only the
+   diagonal) and the COCG residuals of all the shifted systems stay collinear
+   with the seed's (r_e = r / pi_e); one operator application per iteration
+   serves the whole window -- the linear-solve counterpart of obtaining G over
+   the whole energy range from one decomposition (Sec. II.C).  The seed E_s is
+   the energy nearest the middle of the window.  FP64 only (the mixed mode's
+   true-residual replacements would break the collinearity): opts->precision
+   must be RSN_FP64, else RSN_EINVAL.  A shift stops once its recurrence
+   residual ||r|| / |pi_e| is at most tol ||b||; shifts that have not within
+   max_iter seed iterations are solved again by the plain FP64 path.
+   x_dev: device, [n_e][n_cols][N] complex128 (as rsn_solve_columns).
+   iters (host, n_e*n_cols, may be NULL): seed iterations at which each shift
+   converged (or the plain path's count; < 0 if that failed too); relres (may
+   be NULL): the recurrence estimate of the relative residual.
+   Memory: the shifted directions take n_e * N complex128 per column in flight.
+   Errors: as rsn_solve_columns. */
+rsn_status rsn_solve_columns_shifted(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                                     const int32_t* cols, const rsn_solver_opts* opts,
+                                     void* x_dev, int32_t* iters, double* relres);
+
+/* T(E) over an energy window by shifted COCG (as rsn_solve_columns_shifted):
+   the shifted iterates are kept only on the support of Gamma_L, which is all
+   Eq. T-realspace reads, T[e] = 4 sum_c Gamma_R[cols[c]] sum_{i in L}
+   Gamma_L,i |x_{e,c}(i)|^2 (FP64, fixed order).  T: host, n_e doubles; iters
+   as above (may be NULL).  Errors: as rsn_transmission; RSN_EINVAL if
+   Gamma_L is zero everywhere. */
+rsn_status rsn_transmission_shifted(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                                    const int32_t* cols, const rsn_solver_opts* opts, double* T,
+                                    int32_t* iters);
+
+/* T(E) as rsn_transmission, keeping the forward columns: x_dev (device,
+   [n_e][n_cols][N] complex128, caller-owned) receives x_{e,c} = G(E[e]) e_{cols[c]}
+   so that a later rsn_transmission_vjp_reuse needs only the adjoint solves.
+   T: host, n_e doubles.  Errors: as rsn_transmission. */
+rsn_status rsn_transmission_keep(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                                 const int32_t* cols, const rsn_solver_opts* opts, void* x_dev,
+                                 double* T);
+
+/* Vector-Jacobian product of T with respect to V_loc from given forward columns
+   (as written by rsn_transmission_keep with the same E, cols and potential):
+   dV[r] = sum_e T_bar[e] 8 sum_c Gamma_R,c Re(lambda_{e,c}(r) x_{e,c}(r)) with one
+   adjoint solve lambda = G (Gamma_L o conj(x)) per column (G^T = G, Eq.
+   complex-sym) -- the forward columns are reused, not solved again.
+   x_dev: device [n_e][n_cols][N] complex128, read only.  dV: host or device
+   (dV_is_device) N doubles, overwritten.  Errors: as rsn_transmission_vjp. */
+rsn_status rsn_transmission_vjp_reuse(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                                      const int32_t* cols, const rsn_solver_opts* opts,
+                                      const void* x_dev, const double* T_bar, double* dV,
+                                      int dV_is_device);
+
 /* T(E) of several junctions at once (many junctions, energies and column sets
    of uneven sizes; each junction is Eq. T-realspace on its own context):
    ctxs[k] holds junction k (distinct contexts, all set up); it gets n_e[k]
@@ -236,27 +298,32 @@ rsn_status rsn_bench_kernel(rsn_ctx* ctx, int precision, int kind, int nslots, i
                             double* ms_per_launch, double* bytes_per_launch);
 
 /* Autotuner: times the fused operator kernel (rsn_bench_kernel kind 0) for a
-   set of tilings of this grid -- the FP32 point-pair kernel and the
-   whole-plane bulk-copy kernel with several z-chunk lengths, and the
+   set of tilings of this grid -- the FP32 plane kernel, the point-pair kernel
+   and the whole-plane bulk-copy kernel with several z-chunk lengths, and the
    register-prefetch kernel over rows per tile, points per thread and z-chunks
    -- and keeps the fastest on the context.  Outputs (any may be NULL): the
-   chosen TY, Lz, ppt (0 = automatic), tma (2: the point-pair kernel, 1: the
-   whole-plane bulk-copy kernel, 0: the register kernel) and its algorithmic
-   GB/s.  Errors: as rsn_bench_kernel; RSN_ECUDA if no candidate ran. */
+   chosen TY, Lz, ppt (0 = automatic), tma (3: the plane kernel, 2: the
+   point-pair kernel, 1: the whole-plane bulk-copy kernel, 0: the register
+   kernel) and its algorithmic GB/s.  Errors: as rsn_bench_kernel; RSN_ECUDA
+   if no candidate ran. */
 rsn_status rsn_autotune(rsn_ctx* ctx, int precision, int nslots, int* TY, int* Lz, int* ppt,
                         int* tma, double* best_gbs);
 
-/* Override the operator kernel's tile (0 = automatic).  Automatic: FP32
-   operators on grids with nx even and planes of at most 1280 points use the
-   point-pair kernel (two x-neighbours per thread, whole planes streamed by bulk
-   copies, Lz planes per CTA); everything else the register-prefetch kernel.
-   TY rows of the x-y plane per CTA and ppt owned points per thread (1..4)
-   select the register-prefetch kernel; ppt = -1 selects the whole-plane
-   bulk-copy kernel with one point per thread (FP32, planes of at most 1024
-   points with 16-byte aligned sizes; other cases keep the register kernel).
-   The FP64 true-residual kernel takes TY and ppt but always works on two
-   planes per CTA.  Used by the autotuner and by tests that force ragged
-   tiles; it does not change results beyond rounding order.
+/* Override the operator kernel's tile (0 = automatic).  Automatic, for FP32
+   operators: with nx even and planes of at most 1280 points, the point-pair
+   kernel (two x-neighbours per thread, whole planes streamed by bulk copies
+   through a ring of shared-memory stages, a register ring of 2R+1 planes,
+   two CTAs per SM up to 576 points); else, for planes of an even number of at
+   most 576 points, the plane kernel (the same with one point per thread);
+   everything else, and FP64, the register-prefetch kernel.  Lz sets the
+   planes per CTA of any of them.  TY rows of the x-y plane per CTA and ppt
+   owned points per thread (1..4) select the register-prefetch kernel; ppt = -1
+   the whole-plane bulk-copy kernel with a shifted register queue (FP32, planes
+   of at most 1024 points with 16-byte aligned sizes); ppt = -2 the point-pair
+   kernel; ppt = -3 the plane kernel.  Cases a choice does not support keep the
+   next kernel in this order.  The FP64 true-residual kernel takes TY and ppt but
+   always works on two planes per CTA.  Used by the autotuner and by tests that
+   force ragged tiles; it does not change results beyond rounding order.
    Errors: RSN_EINVAL. */
 rsn_status rsn_set_tiling(rsn_ctx* ctx, int TY, int Lz, int ppt);
 

@@ -39,6 +39,14 @@ _SIGS = {
                                     ct.c_void_p]),
     "rsn_transmission_vjp": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
                                         ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p]),
+    "rsn_solve_columns_shifted": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
+                                             ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "rsn_transmission_shifted": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
+                                            ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "rsn_transmission_keep": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                         ct.c_void_p, ct.c_void_p]),
+    "rsn_transmission_vjp_reuse": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
+                                              ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
     "rsn_batch_transmission": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                           ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_last_stats": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -66,6 +74,7 @@ class SolverOpts(ct.Structure):
         ("graph_iters", ct.c_int),
         ("timing", ct.c_int),
         ("tol_adjoint", ct.c_double),
+        ("tol_T", ct.c_double),
     ]
 
 
@@ -208,6 +217,36 @@ class Context:
             self._check("rsn_solve_columns", rc)
         return x, iters.reshape(E.size, cols.size), relres.reshape(E.size, cols.size)
 
+    def solve_columns_shifted(self, E: Sequence[float], cols: Sequence[int], opts: Optional[SolverOpts] = None):
+        """Columns at every energy from one Krylov space per column (FP64):
+        (CUDA complex128 tensor (n_e, n_cols, N), iterations, recurrence residuals)."""
+        torch = _torch()
+        opts = opts or default_opts()
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        x = torch.empty((E.size, cols.size, self.N), dtype=torch.complex128, device=f"cuda:{self.device}")
+        iters = np.zeros(E.size * cols.size, np.int32)
+        relres = np.zeros(E.size * cols.size, np.float64)
+        self._check("rsn_solve_columns_shifted",
+                    self.lib.rsn_solve_columns_shifted(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
+                                                       ct.byref(opts), x.data_ptr(), _ptr(iters), _ptr(relres)))
+        return x, iters.reshape(E.size, cols.size), relres.reshape(E.size, cols.size)
+
+    def transmission_shifted(self, E: Sequence[float], cols: Optional[Sequence[int]] = None,
+                             opts: Optional[SolverOpts] = None, return_iters: bool = False):
+        """T(E) over an energy window by shifted COCG (FP64)."""
+        opts = opts or default_opts()
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        if cols is None:
+            cols = self.junction.right_columns()
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        T = np.zeros(E.size, np.float64)
+        iters = np.zeros(E.size * cols.size, np.int32)
+        self._check("rsn_transmission_shifted",
+                    self.lib.rsn_transmission_shifted(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
+                                                      ct.byref(opts), _ptr(T), _ptr(iters)))
+        return (T, iters.reshape(E.size, cols.size)) if return_iters else T
+
     def transmission(self, E: Sequence[float], cols: Optional[Sequence[int]] = None,
                      opts: Optional[SolverOpts] = None) -> np.ndarray:
         opts = opts or default_opts()
@@ -243,6 +282,39 @@ class Context:
                     self.lib.rsn_transmission_vjp(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
                                                   ct.byref(opts), _ptr(Tb), dptr, isdev, _ptr(T)))
         return T, dV
+
+    def transmission_keep(self, E: Sequence[float], cols: Sequence[int], opts: Optional[SolverOpts] = None):
+        """(T(E), forward columns as a CUDA complex128 tensor (n_e, n_cols, N))."""
+        torch = _torch()
+        opts = opts or default_opts()
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        x = torch.empty((E.size, cols.size, self.N), dtype=torch.complex128, device=f"cuda:{self.device}")
+        T = np.zeros(E.size, np.float64)
+        self._check("rsn_transmission_keep",
+                    self.lib.rsn_transmission_keep(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
+                                                   ct.byref(opts), x.data_ptr(), _ptr(T)))
+        return T, x
+
+    def transmission_vjp_reuse(self, E: Sequence[float], T_bar: Sequence[float], cols: Sequence[int], x,
+                               opts: Optional[SolverOpts] = None, dV_out=None):
+        """dV = sum_e T_bar[e] dT(E[e])/dV_loc from the forward columns ``x`` of
+        ``transmission_keep`` (adjoint solves only)."""
+        opts = opts or default_opts()
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        Tb = np.ascontiguousarray(T_bar, dtype=np.float64)
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        if x.shape != (E.size, cols.size, self.N) or not x.is_contiguous():
+            raise ValueError("x must be the (n_e, n_cols, N) columns of transmission_keep")
+        if dV_out is not None:
+            dptr, isdev, dV = dV_out.data_ptr(), 1, dV_out
+        else:
+            dV = np.zeros(self.N, np.float64)
+            dptr, isdev = _ptr(dV), 0
+        self._check("rsn_transmission_vjp_reuse",
+                    self.lib.rsn_transmission_vjp_reuse(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
+                                                        ct.byref(opts), x.data_ptr(), _ptr(Tb), dptr, isdev))
+        return dV
 
     def kernel_stats(self, kind: int):
         """(launches, ms, algorithmic bytes) of kind 0 (COCG operator) / 1 (COCG update)."""

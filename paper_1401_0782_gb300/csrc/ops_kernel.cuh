@@ -129,7 +129,7 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
   C* sm0 = reinterpret_cast<C*>(smem_raw);
   C* sm1 = sm0 + rows * pitch;
   C* ce = sm1 + rows * pitch;
-  __shared__ double red[32 * 3];
+  __shared__ double red[32 * 4];
 
   for (int i = tid; i < 2 * rows * pitch; i += nt) sm0[i] = czero<C>();
 
@@ -241,6 +241,7 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
   }
 
   CT acc0 = 0, acc1 = 0, acc2 = 0;  // COCG: mu(re,im) ; RESID: nrm, rho(re,im)
+  double acc3 = 0.0;                // RESID: sum Gamma_L |v|^2 of the iterate (T partial)
   CT car0 = 0, car1 = 0;            // Kahan carries of the COCG sums
   // per-point operator data of the next plane to compute, loaded one plane early
   float2 dgf_n[PPT];
@@ -348,6 +349,10 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
         acc0 = fma(rx, rx, fma(ry, ry, acc0));
         acc1 = fma(rx, rx, fma(-ry, ry, acc1));
         acc2 = fma(2.0 * rx, ry, acc2);
+        if (col >= 0) {
+          const double g = J.gl[gl];
+          acc3 = fma(g, (double)vc.x * vc.x + (double)vc.y * vc.y, acc3);
+        }
       } else {
         reinterpret_cast<CO*>(y_out)[vo + gl] = from64<CO>(to64(y));
       }
@@ -360,10 +365,11 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
     block_sum<2>(v, red, out);
     if (tid == 0) b.mu_part[(size_t)s * b.PA + tile] = make_double2(out[0], out[1]);
   } else if constexpr (MODE == OP_RESID) {
-    CT v[3] = {acc0, acc1, acc2};
-    double out[3];
-    block_sum<3>(v, red, out);
+    CT v[4] = {acc0, acc1, acc2, acc3};
+    double out[4];
+    block_sum<4>(v, red, out);
     if (tid == 0) {
+      b.t0_part[(size_t)s * b.PA + tile] = out[3];
       b.nrm0_part[(size_t)s * b.PA + tile] = out[0];
       b.rho0_part[(size_t)s * b.PA + tile] = make_double2(out[1], out[2]);
     }
@@ -649,6 +655,11 @@ cudaError_t launch_op_tma_r(int mode, bool fp32, dim3 grid, int threads, size_t 
                                  cudaStream_t st, const JuncDev* jt, const BatchDev* b,         \
                                  const void* x_in, void* y_out, const void* c_in) {              \
     return launch_op_tma_r<R>(mode, fp32, grid, threads, smem, st, jt, b, x_in, y_out, c_in);    \
+  }                                                                                               \
+  cudaError_t launch_op_plane_R##R(int mode, dim3 grid, int threads, size_t smem, cudaStream_t st, \
+                                   const JuncDev* jt, const BatchDev* b, const void* x_in,      \
+                                   void* y_out, const void* c_in) {                              \
+    return launch_op_plane_r<R>(mode, grid, threads, smem, st, jt, b, x_in, y_out, c_in);        \
   }                                                                                               \
   cudaError_t launch_op_pair_R##R(int mode, bool big, dim3 grid, int threads, size_t smem,        \
                                   cudaStream_t st, const JuncDev* jt, const BatchDev* b,        \

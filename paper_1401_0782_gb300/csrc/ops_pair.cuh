@@ -17,8 +17,6 @@
 //    the x and y neighbours (one barrier per plane), whose row pitch nx + 16 lets
 //    a quarter warp that crosses a row boundary still touch 32 distinct banks;
 //    the zero columns and rows around it are the Dirichlet boundary.
-//  * Complex arithmetic uses Blackwell's paired FP32 instructions (add / sub /
-//    fma .f32x2): one instruction per complex add.
 //
 // FP32 accuracy: the neighbour terms at distances m <= 2, whose weights carry
 // the large part of the Laplacian, are summed in difference form,
@@ -33,46 +31,26 @@
 
 namespace rsn {
 
-// elementwise a + b, a - b, a * b + c on (re, im) pairs: one paired-FP32
-// instruction each, operands packed into 64-bit registers inside the asm
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-  float2 d;
-  asm("{.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\t"
-      "mov.b64 rb, {%4, %5};\n\t"
-      "add.rn.f32x2 rd, ra, rb;\n\t"
-      "mov.b64 {%0, %1}, rd;}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  float2 d;
-  asm("{.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\t"
-      "mov.b64 rb, {%4, %5};\n\t"
-      "sub.rn.f32x2 rd, ra, rb;\n\t"
-      "mov.b64 {%0, %1}, rd;}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
+// elementwise a + b, a - b, a * b + c on (re, im) pairs (the compiler pairs
+// them into Blackwell's two-wide FP32 instructions where that pays; explicit
+// f32x2 inline assembly measured slower, its operand packing costs moves)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\t"
-      "mov.b64 rb, {%4, %5};\n\t"
-      "mov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
-      "mov.b64 {%0, %1}, rd;}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
 }
 // acc + a * b for complex a, b
 __device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 acc) {
   acc = fma2(make_float2(a.x, a.x), b, acc);
   return fma2(make_float2(-a.y, a.y), make_float2(b.y, b.x), acc);
+}
+
+// Kahan-compensated accumulation (sum, carry) for long FP32 dot products.
+__device__ __forceinline__ void kahan_add_f(float& sum, float& carry, float term) {
+  const float y = term - carry;
+  const float t = sum + y;
+  carry = (t - sum) - y;
+  sum = t;
 }
 
 struct Pair {
@@ -91,7 +69,7 @@ __device__ __forceinline__ void sts_pair(float2* s, const Pair& v) {
 
 
 template <int R, int MODE, bool BIG>
-__global__ void __maxnreg__(BIG ? 96 : 112)
+__global__ void __maxnreg__(96)
 op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const void* __restrict__ x_in,
                void* __restrict__ y_out, const void* __restrict__ c_in) {
   constexpr int Q = 2 * R + 1;
@@ -187,14 +165,18 @@ op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, 
   const int po = x0 + yl * nx;                     // offset within a plane (even)
   const int so = (yl + R) * pitch + x0 + kPairXO;  // exchange-tile index of the pair (even)
 
-  float wst[R + 1];
-  float dshift = 0.f;  // -6 sum_{m > MD} w_m: the direct terms' share of the diagonal
-#pragma unroll
-  for (int m = 1; m <= R; ++m) {
-    wst[m] = J.w32[m];
-    if (m > MD) dshift -= 6.f * J.w32[m];
+  // FD weights and E - 6 sum_{m > MD} w_m (the direct terms' share of the
+  // diagonal) in shared memory: broadcast reads instead of live registers
+  __shared__ float s_w[R + 2];
+  if (tid == 0) {
+    float dshift = 0.f;
+    for (int m = 1; m <= R; ++m) {
+      s_w[m] = J.w32[m];
+      if (m > MD) dshift -= 6.f * J.w32[m];
+    }
+    s_w[0] = (float)b.E[s] + dshift;
   }
-  const float Ef = (float)b.E[s] + dshift;
+  __syncthreads();
   const float4* dg4 = reinterpret_cast<const float4*>(J.dg32);
   float4 dgn = make_float4(0.f, 0.f, 0.f, 0.f);  // (-V_loc, Gamma) of both points of the next plane
   if (own && z0 < z1) dgn = __ldg(dg4 + ((z0 * plane + po) >> 1));
@@ -270,7 +252,7 @@ op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, 
             const Pair ym = lds_pair(smb + so - m * pitch), yp = lds_pair(smb + so + m * pitch);
             const float2 xm0 = X[2 * KX - m], xp0 = X[2 * KX + m];
             const float2 xm1 = X[2 * KX + 1 - m], xp1 = X[2 * KX + 1 + m];
-            const float2 w = make_float2(wst[m], wst[m]);
+            const float2 w = make_float2(s_w[m], s_w[m]);
             float2 s0, s1;
             if (m <= MD) {
               s0 = add2(add2(add2(sub2(zm.a, c0), sub2(zp.a, c0)), add2(sub2(ym.a, c0), sub2(yp.a, c0))),
@@ -285,6 +267,7 @@ op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, 
             lap1 = fma2(w, s1, lap1);
           }
           // + (E - V_loc + dshift + i Gamma) v
+          const float Ef = s_w[0];
           float2 y0v = cfma2(make_float2(Ef + dgc.x, dgc.y), c0, lap0);
           float2 y1v = cfma2(make_float2(Ef + dgc.z, dgc.w), c1, lap1);
           const int gi = zc * plane + po;
@@ -333,6 +316,245 @@ op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, 
     block_sum<2>(vv, red, out);
     if (tid == 0) b.mu_part[(size_t)s * b.PA + tile] = make_double2(out[0], out[1]);
   }
+}
+
+// ---------------------------------------------------------------------------
+// One point per thread, whole planes streamed by bulk copies: the same march
+// as op_pair_kernel (bulk-copied input planes, register ring of 2R+1 produced
+// planes unrolled by 2R+1, double-buffered exchange tile, hybrid difference
+// form) with one grid point per thread, so that the z ring takes 2R+1 complex
+// values and two CTAs of up to kPlaneThreads threads fit one SM.  Any nx; the
+// plane size must be even (16-byte bulk copies).
+// ---------------------------------------------------------------------------
+template <int R, int MODE>
+__global__ void __launch_bounds__(kPlaneThreads, 2)
+op_plane_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, const void* __restrict__ x_in,
+                void* __restrict__ y_out, const void* __restrict__ c_in) {
+  constexpr int Q = 2 * R + 1;
+  constexpr int MD = R < 2 ? R : 2;  // distances summed in difference form
+  constexpr int NIN = (MODE == OP_COCG) ? 2 : 1;
+  const BatchDev& b = *bp;
+  const int s = blockIdx.y;
+  if constexpr (MODE == OP_COCG) {
+    if (b.state[s] != SL_ACTIVE) return;
+  }
+  const JuncDev& J = jt[b.junc[s]];
+  const int tile = blockIdx.x;
+  if (tile >= J.nA) return;
+
+  const int nx = J.nx, ny = J.ny, nz = J.nz, plane = J.plane;
+  const int z0 = tile * J.Lz, z1 = min(z0 + J.Lz, nz);
+  const int pitch = nx + 2 * kPairXO;
+  const int rows = ny + 2 * R;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long vo = b.voff[s];
+  const int n_proj = J.n_proj;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* stage = reinterpret_cast<float2*>(smem_raw);  // [kPairStages][NIN][plane]
+  float2* exch = stage + kPairStages * NIN * plane;    // [2][rows][pitch]
+  float2* ce = exch + 2 * rows * pitch;                 // apply mode: e_kb[p] (v_p . x)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(ce + (MODE == OP_APPLY ? n_proj + kCePad : 0)) + 15) &
+      ~static_cast<uintptr_t>(15));
+  __shared__ double red[32 * 2];
+  __shared__ int s_bad;
+  __shared__ float s_w[R + 2];
+
+  for (int i = tid; i < 2 * rows * pitch; i += nt) exch[i] = make_float2(0.f, 0.f);
+  if (tid == 0) {
+    for (int k = 0; k < kPairStages; ++k) mbar_init(bars + k, 1);
+    s_bad = 0;
+    // FD weights and E - 6 sum_{m > MD} w_m (the direct terms' share of the diagonal)
+    float dshift = 0.f;
+    for (int m = 1; m <= R; ++m) {
+      s_w[m] = J.w32[m];
+      if (m > MD) dshift -= 6.f * J.w32[m];
+    }
+    s_w[0] = (float)b.E[s] + dshift;
+  }
+
+  const int k = (MODE == OP_COCG) ? b.iters[s] : 0;
+  const bool first = (MODE == OP_COCG) && (k == 0);
+  float2 beta = make_float2(0.f, 0.f);
+  if (MODE == OP_COCG && !first) beta = make_float2((float)b.beta_cur[s].x, (float)b.beta_cur[s].y);
+  const float2* src0;
+  const float2* src1 = nullptr;
+  float2* pnew = nullptr;
+  float2* yv;
+  if constexpr (MODE == OP_COCG) {
+    src0 = reinterpret_cast<const float2*>(b.r) + vo;
+    if (!first) src1 = reinterpret_cast<const float2*>((k & 1) ? b.p1 : b.p0) + vo;
+    pnew = reinterpret_cast<float2*>((k & 1) ? b.p0 : b.p1) + vo;
+    yv = reinterpret_cast<float2*>(b.q) + vo;
+  } else {
+    src0 = reinterpret_cast<const float2*>(x_in) + vo;
+    yv = reinterpret_cast<float2*>(y_out) + vo;
+  }
+  if (MODE == OP_APPLY && n_proj > 0) {
+    const float2* cin = reinterpret_cast<const float2*>(c_in) + (size_t)s * n_proj;
+    for (int p = tid; p < n_proj; p += nt) {
+      const float e = (float)J.ekb[p];
+      const float2 c = cin[p];
+      ce[p] = make_float2(e * c.x, e * c.y);
+    }
+    for (int p = tid; p < kCePad; p += nt) ce[n_proj + p] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+
+  const int zb = z0 - R, ze = z1 + R;
+  const uint32_t pbytes = (uint32_t)(plane * sizeof(float2));
+  auto issue = [&](int zl) {
+    const int st = (zl - zb) % kPairStages;
+    uint64_t* bar = bars + st;
+    if (zl >= 0 && zl < nz) {
+      mbar_arrive_expect_tx(bar, src1 ? 2 * pbytes : pbytes);
+      bulk_g2s(stage + (st * NIN) * plane, src0 + (size_t)zl * plane, pbytes, bar);
+      if (src1) bulk_g2s(stage + (st * NIN + 1) * plane, src1 + (size_t)zl * plane, pbytes, bar);
+    } else {
+      mbar_arrive(bar);
+    }
+  };
+  if (tid == 0) {
+    fence_proxy_async();
+    for (int f = 0; f < kPairStages && zb + f < ze; ++f) issue(zb + f);
+  }
+
+  const bool own = tid < plane;
+  const int yl = own ? tid / nx : 0;
+  const int xl = own ? tid - yl * nx : 0;
+  const int so = (yl + R) * pitch + xl + kPairXO;  // exchange-tile index of the point
+
+  float2 dgn = make_float2(0.f, 0.f);  // (-V_loc, Gamma) of the next plane to compute
+  if (own && z0 < z1) dgn = __ldg(J.dg32 + (z0 * plane + tid));
+
+  float2 zq[Q];
+#pragma unroll
+  for (int m = 0; m < Q; ++m) zq[m] = make_float2(0.f, 0.f);
+  float ma_x = 0.f, ma_y = 0.f, mc_x = 0.f, mc_y = 0.f;  // Kahan sum of mu = v^T A_loc v
+  int sidx = 0;
+  uint32_t sph = 0;
+
+  for (int zr = z0 - 2 * R; zr < z1; zr += Q) {
+#pragma unroll
+    for (int u = 0; u < Q; ++u) {
+      const int zc = zr + u;
+      if (zc < z1) {
+        const int zl = zc + R;
+        float2 v = make_float2(0.f, 0.f);
+        if (!mbar_wait(bars + sidx, sph)) {
+          s_bad = 1;
+        } else if (own && zl >= 0 && zl < nz) {
+          v = stage[(sidx * NIN) * plane + tid];
+          if constexpr (MODE == OP_COCG) {
+            if (src1) {
+              const float2 pp = stage[(sidx * NIN + 1) * plane + tid];
+              v.x = fmaf(beta.x, pp.x, fmaf(-beta.y, pp.y, v.x));
+              v.y = fmaf(beta.x, pp.y, fmaf(beta.y, pp.x, v.y));
+            }
+          }
+        }
+        zq[u] = v;
+        const int C = (u + R + 1) % Q;  // ring slot of plane zc (a constant once unrolled)
+        float2* smb = exch + (((zc - z0) & 1) ? rows * pitch : 0);
+        if (zc >= z0 && own) smb[so] = zq[C];
+        __syncthreads();
+        if (s_bad) {
+          if (tid == 0) {
+            atomicExch(b.sched + 2, 1);
+            for (int f = 0; f < kPairStages; ++f) {
+              const int zq2 = zl + f;
+              if (zq2 < ze) mbar_wait(bars + (zq2 - zb) % kPairStages, (uint32_t)(((zq2 - zb) / kPairStages) & 1));
+            }
+          }
+          return;
+        }
+        if (tid == 0 && zl + kPairStages < ze) {
+          fence_proxy_async();
+          issue(zl + kPairStages);
+        }
+        if (++sidx == kPairStages) {
+          sidx = 0;
+          sph ^= 1u;
+        }
+        if (zc >= z0 && own) {
+          const float2 dgc = dgn;
+          if (zc + 1 < z1) dgn = __ldg(J.dg32 + ((zc + 1) * plane + tid));
+          const float2 c = zq[C];
+          float lx = 0.f, ly = 0.f;
+#pragma unroll
+          for (int m = 1; m <= R; ++m) {
+            const float2 zm = zq[(C + Q - m) % Q], zp = zq[(C + m) % Q];
+            const float2 ym = smb[so - m * pitch], yp = smb[so + m * pitch];
+            const float2 xm = smb[so - m], xp = smb[so + m];
+            const float w = s_w[m];
+            float sx, sy;
+            if (m <= MD) {
+              sx = ((zm.x - c.x) + (zp.x - c.x)) + ((ym.x - c.x) + (yp.x - c.x)) + ((xm.x - c.x) + (xp.x - c.x));
+              sy = ((zm.y - c.y) + (zp.y - c.y)) + ((ym.y - c.y) + (yp.y - c.y)) + ((xm.y - c.y) + (xp.y - c.y));
+            } else {
+              sx = ((zm.x + zp.x) + (ym.x + yp.x)) + (xm.x + xp.x);
+              sy = ((zm.y + zp.y) + (ym.y + yp.y)) + (xm.y + xp.y);
+            }
+            lx = fmaf(w, sx, lx);
+            ly = fmaf(w, sy, ly);
+          }
+          // + (E - V_loc + dshift + i Gamma) v
+          const float dr = s_w[0] + dgc.x, di = dgc.y;
+          float2 y = make_float2(fmaf(dr, c.x, fmaf(-di, c.y, lx)), fmaf(dr, c.y, fmaf(di, c.x, ly)));
+          const int gi = zc * plane + tid;
+          if constexpr (MODE == OP_APPLY) {
+            if (n_proj > 0) {
+              const int nq = J.inv_nq;
+              const int e0 = J.inv_ptr[gi], e1 = J.inv_ptr[gi + 1];
+              for (int e = e0; e < e1; ++e) {
+                const float2* cp = ce + J.inv_p0[e];
+                for (int qd = 0; qd < nq; ++qd) {
+                  const float4 a = J.inv_q32[e * nq + qd];
+                  const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                  for (int jj = 0; jj < 4; ++jj) {
+                    y.x = fmaf(-av[jj], cp[4 * qd + jj].x, y.x);
+                    y.y = fmaf(-av[jj], cp[4 * qd + jj].y, y.y);
+                  }
+                }
+              }
+            }
+          }
+          if constexpr (MODE == OP_COCG) {
+            pnew[gi] = c;
+            // mu partial v^T y (unconjugated), Kahan-compensated
+            kahan_add_f(ma_x, mc_x, fmaf(c.x, y.x, -c.y * y.y));
+            kahan_add_f(ma_y, mc_y, fmaf(c.x, y.y, c.y * y.x));
+          }
+          yv[gi] = y;
+        }
+      }
+    }
+  }
+  if constexpr (MODE == OP_COCG) {
+    float vv[2] = {ma_x - mc_x, ma_y - mc_y};
+    double out[2];
+    block_sum<2>(vv, red, out);
+    if (tid == 0) b.mu_part[(size_t)s * b.PA + tile] = make_double2(out[0], out[1]);
+  }
+}
+
+template <int R>
+cudaError_t launch_op_plane_r(int mode, dim3 grid, int threads, size_t smem, cudaStream_t st, const JuncDev* jt,
+                              const BatchDev* b, const void* x_in, void* y_out, const void* c_in) {
+  void (*kern)(const JuncDev*, const BatchDev*, const void*, void*, const void*) = nullptr;
+  if (mode == OP_COCG) kern = op_plane_kernel<R, OP_COCG>;
+  else if (mode == OP_APPLY) kern = op_plane_kernel<R, OP_APPLY>;
+  else return cudaErrorInvalidValue;
+  if (threads > kPlaneThreads) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
+    if (e != cudaSuccess) return e;
+  }
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  kern<<<grid, threads, smem, st>>>(jt, b, x_in, y_out, c_in);
+  return cudaGetLastError();
 }
 
 template <int R>

@@ -62,6 +62,7 @@ struct Tiling {
   size_t smem = 0;
   bool tma = false;   // whole-plane tile streamed by bulk copies (op_kernel_tma)
   bool pair = false;  // FP32 point-pair kernel with plane streaming (op_pair_kernel)
+  bool plane = false; // FP32 one-point-per-thread kernel with plane streaming (op_plane_kernel)
   bool big = false;   // its one-CTA-per-SM variant (planes of more than 2 * kPairThreads points)
 };
 
@@ -74,7 +75,7 @@ struct Workspace {
   DevBuf Xslot, r, p0, p1, q, d;
   DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, stall, warm, rho_cur, beta_cur;
   DevBuf bnorm2, sigma, rlast2, rrec2, tol2;
-  DevBuf rho0, nrm0, rho, nrm, mu, c_r, c_p, c_x, sched, counters, lst, lst_n, fslot, c_e;
+  DevBuf rho0, nrm0, t0, tlast, gcnt, gphase, tgoal, rgoal, rho, nrm, mu, c_r, c_p, c_x, sched, counters, lst, lst_n, fslot, c_e;
   int generation = 0;
 };
 
@@ -83,13 +84,26 @@ struct CallBufs {
   DevBuf sys_junc, sys_E, sys_col, sys_xo, sys_xfo, sys_dep, sys_bn2, sys_started, out_iters, out_relres, out_status,
       out_t;
   DevBuf X0, X1, wt, g, t_all, gr_cols, Td;
+  // shifted systems
+  DevBuf sh_sig, sh_idx, sh_xs, sh_ps, sh_pi, sh_cit, sh_alpha, sh_beta, sh_rn2, sh_ts, sh_sit, sh_srel;
+};
+
+// Shifted-system part of a stream (rsn_*_shifted): the energies' shifts from
+// the seed, the tracked points and where the shifted iterates go.
+struct ShiftSpec {
+  int n_shift = 0;
+  std::vector<double> sig;  // E_e - E_seed
+  int nT = 0;
+  const int* idx = nullptr;  // device: tracked grid points
+  double2* xs_out = nullptr; // caller's [n_e][n_cols][N] output (every point tracked), or null: slot storage
+  long long n_cols = 0;
 };
 
 struct GraphKey {
-  int fp32, slots, iters, generation, proj, timing;
+  int fp32, slots, iters, generation, proj, timing, n_shift, nT;
   bool operator<(const GraphKey& o) const {
-    return std::tie(fp32, slots, iters, generation, proj, timing) <
-           std::tie(o.fp32, o.slots, o.iters, o.generation, o.proj, o.timing);
+    return std::tie(fp32, slots, iters, generation, proj, timing, n_shift, nT) <
+           std::tie(o.fp32, o.slots, o.iters, o.generation, o.proj, o.timing, o.n_shift, o.nT);
   }
 };
 
@@ -183,8 +197,11 @@ static void clear_graphs(rsn_ctx* c) {
 // tiling of the operator kernel
 // ---------------------------------------------------------------------------
 // Tiling overrides (rsn_set_tiling): TY rows, Lz planes, ppt points per
-// thread; ppt = -1 selects the whole-plane bulk-copy kernel, ppt = -2 the FP32
-// point-pair kernel (also the automatic choice where it applies).
+// thread; ppt = -1 selects the whole-plane bulk-copy kernel of one point per
+// thread with a register-shifted queue, ppt = -2 the FP32 point-pair kernel,
+// ppt = -3 the FP32 plane kernel (one point per thread, unrolled ring);
+// automatic: the point-pair kernel where it applies (nx even), else the plane
+// kernel, else the register kernel.
 // `streamable`: the vectors of this launch are 16-byte aligned (bulk copies).
 static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslots, bool streamable = true) {
   Tiling t;
@@ -193,7 +210,17 @@ static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslo
   // FP32 point-pair kernel: whole planes, nx even (16-byte pairs), at most
   // 2 * kPairThreadsBig points per plane, no explicit register tile requested
   const bool reg_forced = c->tile_override[0] > 0 || c->tile_override[2] > 0 || c->tile_override[3] == -1;
-  if (!compute64 && mode != OP_RESID && streamable && !reg_forced && nx % 2 == 0) {
+  auto z_chunks = [&](int per_sm) {
+    int zt = (4 * per_sm * 152 + nslots - 1) / nslots;
+    zt = std::max(1, std::min(zt, std::max(1, nz / (2 * R + 2))));
+    if (c->tile_override[1] > 0) zt = (nz + c->tile_override[1] - 1) / c->tile_override[1];
+    t.Lz = (nz + zt - 1) / zt;
+    t.ztiles = (nz + t.Lz - 1) / t.Lz;
+    t.n = t.ztiles;
+    t.TY = ny;
+    t.ytiles = 1;
+  };
+  if (!compute64 && mode != OP_RESID && streamable && !reg_forced && c->tile_override[3] != -3 && nx % 2 == 0) {
     const int thr = (int)(((pl / 2) + 31) / 32 * 32);
     const size_t sm = op_pair_smem_bytes(mode, R, nx, ny, c->n_proj);
     if (thr <= kPairThreadsBig && sm <= 200 * 1024) {
@@ -201,16 +228,20 @@ static Tiling choose_tiling(const rsn_ctx* c, bool compute64, int mode, int nslo
       t.big = thr > kPairThreads;
       t.threads = thr;
       t.smem = sm;
-      t.TY = ny;
-      t.ytiles = 1;
       t.ppt = 2;
-      const int per_sm = t.big ? 1 : 2;
-      int zt = (4 * per_sm * 152 + nslots - 1) / nslots;
-      zt = std::max(1, std::min(zt, std::max(1, nz / (2 * R + 2))));
-      if (c->tile_override[1] > 0) zt = (nz + c->tile_override[1] - 1) / c->tile_override[1];
-      t.Lz = (nz + zt - 1) / zt;
-      t.ztiles = (nz + t.Lz - 1) / t.Lz;
-      t.n = t.ztiles;
+      z_chunks(t.big ? 1 : 2);
+      return t;
+    }
+  }
+  if (!compute64 && mode != OP_RESID && streamable && !reg_forced && c->tile_override[3] != -2 && pl % 2 == 0 &&
+      pl <= kPlaneThreads) {
+    const size_t sm = op_pair_smem_bytes(mode, R, nx, ny, c->n_proj);
+    if (sm <= 100 * 1024) {
+      t.plane = true;
+      t.threads = (int)((pl + 31) / 32 * 32);
+      t.smem = sm;
+      t.ppt = 1;
+      z_chunks(2);
       return t;
     }
   }
@@ -275,6 +306,7 @@ static cudaError_t launch_inner(const rsn_ctx* c, const Tiling& t, int mode, boo
                                 const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out,
                                 const void* c_in) {
   const dim3 grid(t.n, nslots);
+  if (t.plane) return launch_op_plane(mode, c->R, grid, t.threads, t.smem, st, jt, b, x_in, y_out, c_in);
   if (t.pair) return launch_op_pair(mode, c->R, t.big, grid, t.threads, t.smem, st, jt, b, x_in, y_out, c_in);
   if (t.tma) return launch_op_tma(mode, fp32, c->R, grid, t.threads, t.smem, st, jt, b, x_in, y_out, c_in);
   return launch_op(mode, fp32, c->R, t.ppt, grid, t.threads, t.smem, st, jt, b, x_in, y_out, c_in);
@@ -480,10 +512,12 @@ void rsn_default_opts(int precision, rsn_solver_opts* o) {
     o->tol = 1e-10;
     o->tol_inner = 1e-1;
     o->max_iter = 3000;  // slower systems are handed to the FP64 fallback
+    o->tol_T = 1e-7;
   } else {
     o->tol = 1e-13;
     o->tol_inner = 1e-6;
     o->max_iter = 20000;
+    o->tol_T = 1e-10;
   }
   o->tol_adjoint = 0.0;  // the adjoint systems take tol
   o->max_outer = 64;
@@ -681,12 +715,13 @@ static size_t slot_bytes(const rsn_ctx* c, bool fp32) {
 
 // Slots: enough systems in flight to fill the GPU, few enough (relative to the
 // queue) that the drain at the end of the queue stays short, and within memory.
-static int choose_slots(rsn_ctx* c, const rsn_solver_opts* o, long long nsys, size_t reserved) {
+static int choose_slots(rsn_ctx* c, const rsn_solver_opts* o, long long nsys, size_t reserved,
+                        size_t extra_per_slot = 0) {
   if (o->rhs_block > 0) return (int)std::max<long long>(1, std::min<long long>(o->rhs_block, nsys));
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   const double avail = fr > reserved ? 0.6 * (double)(fr - reserved) : 0.0;
-  long long cap = (long long)(avail / (double)slot_bytes(c, o->precision == RSN_MIXED));
+  long long cap = (long long)(avail / (double)(slot_bytes(c, o->precision == RSN_MIXED) + extra_per_slot));
   cap = std::max<long long>(1, std::min<long long>(cap, 8192));
   // one slot per system up to 2048: a stream then ends with its slowest
   // system instead of with a second wave of systems that waited for slots
@@ -735,6 +770,12 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   RSN_CUDA(c, w.tol2.ensure(sd));
   RSN_CUDA(c, w.rho0.ensure((size_t)S * PA * sizeof(double2)));
   RSN_CUDA(c, w.nrm0.ensure((size_t)S * PA * sizeof(double)));
+  RSN_CUDA(c, w.t0.ensure((size_t)S * PA * sizeof(double)));
+  RSN_CUDA(c, w.tlast.ensure(sd));
+  RSN_CUDA(c, w.gcnt.ensure(si));
+  RSN_CUDA(c, w.gphase.ensure(si));
+  RSN_CUDA(c, w.tgoal.ensure(sd));
+  RSN_CUDA(c, w.rgoal.ensure(sd));
   RSN_CUDA(c, w.mu.ensure((size_t)S * PA * sizeof(double2)));
   RSN_CUDA(c, w.rho.ensure((size_t)S * PB * sizeof(double2)));
   RSN_CUDA(c, w.nrm.ensure((size_t)S * PB * sizeof(double)));
@@ -853,6 +894,12 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.d = w.d.p;
   b.rho0_part = w.rho0.as<double2>();
   b.nrm0_part = w.nrm0.as<double>();
+  b.t0_part = w.t0.as<double>();
+  b.tlast = w.tlast.as<double>();
+  b.gcnt = w.gcnt.as<int>();
+  b.gphase = w.gphase.as<int>();
+  b.tgoal = w.tgoal.as<double>();
+  b.rgoal = w.rgoal.as<double>();
   b.rho_part = w.rho.as<double2>();
   b.nrm_part = w.nrm.as<double>();
   b.mu_part = w.mu.as<double2>();
@@ -868,6 +915,7 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.ce_stride = std::max(1, c->n_proj) + kCePad;
   b.tol = o->tol;
   b.tol_adj = o->tol_adjoint > 0 ? o->tol_adjoint : o->tol;
+  b.tol_T = o->tol_T;
   b.delta = o->tol_inner;
   b.max_iter = o->max_iter;
   b.max_upd = o->max_outer;
@@ -883,10 +931,13 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
 
 static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamIn& in, double2* x64_base,
                              const double2* xf_base, bool want_t, size_t reserved,
-                             std::chrono::steady_clock::time_point t_start, StreamOut& out) {
+                             std::chrono::steady_clock::time_point t_start, StreamOut& out,
+                             const ShiftSpec* sh = nullptr) {
   const long long nsys = (long long)in.E.size();
   const bool fp32 = o->precision == RSN_MIXED;
-  const int S = choose_slots(c, o, nsys, reserved);
+  const int ns = sh ? sh->n_shift : 0;
+  const size_t shift_slot_bytes = sh ? (size_t)ns * sh->nT * sizeof(double2) * (sh->xs_out ? 1 : 2) : 0;
+  const int S = choose_slots(c, o, nsys, reserved, shift_slot_bytes);
   rsn_status rs = ensure_ws(c, fp32, S);
   if (rs != RSN_OK) return rs;
   if ((rs = ensure_calls(c, nsys)) != RSN_OK) return rs;
@@ -928,6 +979,48 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   b.out_relres = q.out_relres.as<double>();
   b.out_status = q.out_status.as<int>();
   b.out_t = want_t ? q.out_t.as<double>() : nullptr;
+  if (sh) {
+    const size_t nT = (size_t)sh->nT;
+    RSN_CUDA(c, q.sh_sig.ensure(ns * sizeof(double)));
+    RSN_CUDA(c, q.sh_ps.ensure((size_t)S * ns * nT * sizeof(double2)));
+    if (!sh->xs_out) RSN_CUDA(c, q.sh_xs.ensure((size_t)S * ns * nT * sizeof(double2)));
+    RSN_CUDA(c, q.sh_pi.ensure(3 * (size_t)S * ns * sizeof(double2)));
+    RSN_CUDA(c, q.sh_cit.ensure((size_t)S * ns * sizeof(int)));
+    RSN_CUDA(c, q.sh_alpha.ensure(2 * (size_t)S * sizeof(double2)));
+    RSN_CUDA(c, q.sh_beta.ensure(2 * (size_t)S * sizeof(double2)));
+    RSN_CUDA(c, q.sh_rn2.ensure((size_t)S * sizeof(double)));
+    RSN_CUDA(c, q.sh_ts.ensure((size_t)nsys * ns * sizeof(double)));
+    RSN_CUDA(c, q.sh_sit.ensure((size_t)nsys * ns * sizeof(int)));
+    RSN_CUDA(c, q.sh_srel.ensure((size_t)nsys * ns * sizeof(double)));
+    RSN_CUDA(c, cudaMemcpyAsync(q.sh_sig.p, sh->sig.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    RSN_CUDA(c, cudaMemsetAsync(q.sh_sit.p, 0xff, (size_t)nsys * ns * sizeof(int), st));
+    RSN_CUDA(c, cudaMemsetAsync(q.sh_srel.p, 0, (size_t)nsys * ns * sizeof(double), st));
+    RSN_CUDA(c, cudaMemsetAsync(q.sh_ts.p, 0, (size_t)nsys * ns * sizeof(double), st));
+    b.n_shift = ns;
+    b.shift_sig = q.sh_sig.as<double>();
+    b.nT = sh->nT;
+    b.T_idx = sh->idx;
+    if (sh->xs_out) {
+      b.xs = sh->xs_out;
+      b.xs_by_sys = 1;
+      b.xs_sstride = (long long)nT;             // system = column c
+      b.xs_estride = sh->n_cols * (long long)nT;  // [n_e][n_cols][N]
+    } else {
+      b.xs = q.sh_xs.as<double2>();
+      b.xs_by_sys = 0;
+      b.xs_sstride = (long long)ns * nT;
+      b.xs_estride = (long long)nT;
+    }
+    b.ps = q.sh_ps.as<double2>();
+    b.spi = q.sh_pi.as<double2>();
+    b.sconv_it = q.sh_cit.as<int>();
+    b.salpha = q.sh_alpha.as<double2>();
+    b.sbeta = q.sh_beta.as<double2>();
+    b.rn2 = q.sh_rn2.as<double>();
+    b.out_ts = q.sh_ts.as<double>();
+    b.out_sit = q.sh_sit.as<int>();
+    b.out_srel = q.sh_srel.as<double>();
+  }
   RSN_CUDA(c, cudaMemcpyAsync(c->bd.p, &b, sizeof(b), cudaMemcpyHostToDevice, st));
   const BatchDev* bdev = c->bd.as<BatchDev>();
 
@@ -938,6 +1031,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   const int nB = c->jh.nB;
   const bool proj = c->n_proj > 0;
   const int KL = std::min(S, kListRows);
+  const bool goal = o->tol_T > 0 && !sh;
   const dim3 gr(cfg.resid.n, KL);
   const int G = std::max(1, std::min(kMaxGraphIters, o->graph_iters));
   const bool timing = o->timing != 0;
@@ -953,14 +1047,17 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       cudaError_t e;
       if ((e = launch_list(st, bdev)) != cudaSuccess) return e;
       if ((e = launch_zero(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
+      if (sh && (e = launch_shift_init(sh->nT, st, jr, bdev)) != cudaSuccess) return e;
       if (proj && (e = launch_project(1, fp32, KL, c->n_groups, c->max_np, st, jr, bdev, nullptr, w.c_x.p)) != cudaSuccess)
         return e;
       if ((e = launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, bdev,
                          nullptr, nullptr, nullptr)) != cudaSuccess)
         return e;
       if ((e = launch_x_update(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
+      if (goal && (e = launch_tgoal(st, jr, bdev)) != cudaSuccess) return e;
       if ((e = launch_sched(S, it, st, jr, bdev)) != cudaSuccess) return e;
       if ((e = launch_emit(S, st, jr, bdev)) != cudaSuccess) return e;
+      if (sh && (e = launch_shift_emit(S, ns, st, jr, bdev)) != cudaSuccess) return e;
       if (proj && (e = launch_project(0, fp32, S, c->n_groups, c->max_np, st, ji, bdev, nullptr, w.c_r.p)) != cudaSuccess)
         return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it], st, evf)) != cudaSuccess) return e;
@@ -971,14 +1068,15 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       if ((e = launch_cocg_update(fp32, S, nB, st, ji, bdev)) != cudaSuccess) return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 2], st, evf)) != cudaSuccess) return e;
       if ((e = launch_book(S, it, st, ji, bdev)) != cudaSuccess) return e;
+      if (sh && (e = launch_shift_update(S, sh->nT, ns, st, ji, bdev)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   };
-  const int per_iter = proj ? 12 : 9;
+  const int per_iter = (proj ? 12 : 9) + (sh ? 3 : 0) + (goal ? 1 : 0);
   const double vbytes = (double)N * (fp32 ? sizeof(float2) : sizeof(double2));
   cudaGraphExec_t gexec = nullptr;
   if (o->use_graph) {
-    GraphKey key{fp32 ? 1 : 0, S, G, w.generation, proj ? 1 : 0, timing ? 1 : 0};
+    GraphKey key{fp32 ? 1 : 0, S, G, w.generation, proj ? 1 : 0, timing ? 1 : 0, ns, (sh ? sh->nT : 0) * 2 + (goal ? 1 : 0)};
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
       gexec = it->second;
@@ -1118,7 +1216,7 @@ static rsn_status check_solve_args(rsn_ctx* c, int n_e, const double* E, int n_c
   if (n_e < 0 || n_cols < 0) RSN_FAIL(c, RSN_EINVAL, "negative sizes");
   if ((n_e > 0 && !E) || (n_cols > 0 && !cols) || !o) RSN_FAIL(c, RSN_EINVAL, "NULL argument");
   if (o->precision != RSN_FP64 && o->precision != RSN_MIXED) RSN_FAIL(c, RSN_EINVAL, "bad precision");
-  if (!(o->tol > 0) || !(o->tol_adjoint >= 0) || !(o->tol_inner > 0) || !(o->tol_inner < 1) || o->max_iter < 1 || o->max_outer < 1 ||
+  if (!(o->tol > 0) || !(o->tol_adjoint >= 0) || !(o->tol_T >= 0) || !(o->tol_inner > 0) || !(o->tol_inner < 1) || o->max_iter < 1 || o->max_outer < 1 ||
       o->graph_iters < 0 || o->rhs_block < 0)
     RSN_FAIL(c, RSN_EINVAL, "bad solver options");
   for (int e = 0; e < n_e; ++e)
@@ -1227,6 +1325,7 @@ rsn_status rsn_solve_columns(rsn_ctx* c, int n_e, const double* E, int n_cols, c
       rsn_default_opts(RSN_FP64, &o64);
       o64.tol = o->tol;
       o64.tol_adjoint = o->tol_adjoint;
+      o64.tol_T = o->tol_T;
       o64.deadline_ms = o->deadline_ms;
       o64.use_graph = o->use_graph;
       o64.graph_iters = o->graph_iters;
@@ -1254,14 +1353,20 @@ rsn_status rsn_solve_columns(rsn_ctx* c, int n_e, const double* E, int n_cols, c
   return RSN_OK;
 }
 
-// Shared driver of rsn_transmission and rsn_transmission_vjp.
+// Shared driver of the transmission entry points.
+//  x_keep (not NULL, T only): the forward columns are written to x_keep
+//    [n_e][n_cols][N] (complex128) as well;
+//  x_given (not NULL, with dV): the forward columns are taken from x_given
+//    [n_e][n_cols][N] and only the adjoint systems are solved;
+//  dV (not NULL): vector-Jacobian product sum_e T_bar[e] dT(E[e])/dV_loc.
 static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols,
                                     const rsn_solver_opts* o, const double* T_bar, double* dV, int dV_dev,
-                                    double* T) {
+                                    double* T, double2* x_keep = nullptr, const double2* x_given = nullptr) {
   rsn_status rs = commit_setup(c);
   if (rs != RSN_OK) return rs;
   if ((rs = check_solve_args(c, n_e, E, n_cols, cols, o)) != RSN_OK) return rs;
   const bool adjoint = dV != nullptr;
+  const bool reuse = adjoint && x_given != nullptr;
   if (adjoint && n_e > 0 && !T_bar) RSN_FAIL(c, RSN_EINVAL, "T_bar is NULL");
   if ((rs = enter(c)) != RSN_OK) return rs;
   reset_stats(c);
@@ -1280,41 +1385,49 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
   RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
   rsn_status worst = RSN_OK;
   std::string why;
-  // energies per chunk: the adjoint keeps the forward and adjoint solutions of a
-  // chunk (2 * chunk * n_cols * N complex128) resident
+  // energies per chunk: the adjoint keeps the solutions of a chunk resident
+  // (forward and adjoint: 2 * chunk * n_cols * N complex128; adjoint only when
+  // the forward columns are given)
   int chunk = n_e;
   if (adjoint && n_cols > 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    const double per_e = 2.0 * n_cols * (double)N * sizeof(double2);
+    const double per_e = (reuse ? 1.0 : 2.0) * n_cols * (double)N * sizeof(double2);
     chunk = (int)std::max(1.0, std::min((double)n_e, 0.45 * (double)fr / per_e));
   }
   for (int e0 = 0; e0 < n_e && n_cols > 0; e0 += chunk) {
     const int ne = std::min(chunk, n_e - e0);
     const long long M = (long long)ne * n_cols;
+    // systems: [forward M][adjoint M], [forward M] (T only) or [adjoint M] (reuse)
+    const long long F0 = reuse ? 0 : M;      // forward systems
+    const long long NS = adjoint ? F0 + M : M;
     StreamIn in;
-    in.resize(adjoint ? 2 * M : M);
-    for (long long k = 0; k < M; ++k) {
+    in.resize(NS);
+    for (long long k = 0; k < F0; ++k) {
       in.E[k] = E[e0 + k / n_cols];
       in.col[k] = cols[k % n_cols];
-      in.xo[k] = adjoint ? k * N : -1;
-      if (adjoint) {
-        in.E[M + k] = in.E[k];
-        in.col[M + k] = -1;
-        in.xo[M + k] = (M + k) * N;
-        in.xfo[M + k] = k * N;
-        in.dep[M + k] = (int)k;
-      }
+      in.xo[k] = adjoint ? k * N : (x_keep ? k * N : -1);
     }
+    if (adjoint)
+      for (long long k = 0; k < M; ++k) {
+        in.E[F0 + k] = E[e0 + k / n_cols];
+        in.col[F0 + k] = -1;
+        in.xo[F0 + k] = (F0 + k) * N;
+        in.xfo[F0 + k] = reuse ? (long long)e0 * n_cols * N + k * N : k * N;
+        in.dep[F0 + k] = reuse ? -1 : (int)k;
+      }
     double2* X = nullptr;
+    const double2* XF = nullptr;
     size_t reserved = 0;
     if (adjoint) {
-      RSN_CUDA(c, q.X0.ensure((size_t)(2 * M) * N * sizeof(double2)));
+      RSN_CUDA(c, q.X0.ensure((size_t)NS * N * sizeof(double2)));
       X = q.X0.as<double2>();
+      XF = reuse ? x_given : X;
+    } else if (x_keep) {
+      X = x_keep + (size_t)e0 * n_cols * N;
     }
     StreamOut so;
-    if ((rs = run_stream(c, o, in, X, X, true, reserved, t_start, so)) != RSN_OK) return rs;
-    const long long NS = (long long)in.E.size();
+    if ((rs = run_stream(c, o, in, X, XF, true, reserved, t_start, so)) != RSN_OK) return rs;
     RSN_CUDA(c, q.t_all.ensure(NS * sizeof(double)));
     RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, q.out_t.p, NS * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     if (o->precision == RSN_MIXED) {
@@ -1324,7 +1437,7 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
       std::vector<long long> F;
       StreamIn sub;
       std::vector<int> pos(NS, -1);
-      for (long long k = 0; k < (adjoint ? M : NS); ++k)
+      for (long long k = 0; k < F0; ++k)
         if (so.status[k] != 0) {
           pos[k] = (int)F.size();
           F.push_back(k);
@@ -1332,28 +1445,29 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
           sub.bn2.back() = 0.0;  // cold start (see solve_columns)
         }
       if (adjoint)
-        for (long long k = M; k < 2 * M; ++k)
-          if (so.status[k] != 0 || pos[k - M] >= 0) {
+        for (long long k = F0; k < NS; ++k)
+          if (so.status[k] != 0 || (!reuse && pos[k - F0] >= 0)) {
             F.push_back(k);
             sub.push(in, (size_t)k);
             sub.bn2.back() = 0.0;  // cold start (the right-hand side may have changed)
-            sub.dep.back() = pos[k - M];
+            sub.dep.back() = reuse ? -1 : pos[k - F0];
           }
       if (!F.empty()) {
         rsn_solver_opts o64;
         rsn_default_opts(RSN_FP64, &o64);
         o64.tol = o->tol;
         o64.tol_adjoint = o->tol_adjoint;
+        o64.tol_T = o->tol_T;
         o64.deadline_ms = o->deadline_ms;
         o64.use_graph = o->use_graph;
         o64.graph_iters = o->graph_iters;
         StreamOut s2;
-        if ((rs = run_stream(c, &o64, sub, X, X, true, reserved, t_start, s2)) != RSN_OK) return rs;
+        if ((rs = run_stream(c, &o64, sub, X, XF, true, reserved, t_start, s2)) != RSN_OK) return rs;
         for (size_t f = 0; f < F.size(); ++f) {
           so.status[F[f]] = s2.status[f];
           so.iters[F[f]] += s2.iters[f];
           so.relres[F[f]] = s2.relres[f];
-          if (F[f] < M || !adjoint)
+          if (F[f] < F0)
             RSN_CUDA(c, cudaMemcpyAsync(q.t_all.as<double>() + F[f], q.out_t.as<double>() + f, sizeof(double),
                                         cudaMemcpyDeviceToDevice, c->st));
         }
@@ -1361,26 +1475,29 @@ static rsn_status transmission_impl(rsn_ctx* c, int n_e, const double* E, int n_
       }
     }
     std::string w1;
-    rsn_status bs = stream_status(so, 0, (long long)in.E.size(), nullptr, nullptr, &w1);
+    rsn_status bs = stream_status(so, 0, NS, nullptr, nullptr, &w1);
     if (worst == RSN_OK && bs != RSN_OK) {
       worst = bs;
-      why = (adjoint ? "(forward systems 0.." + std::to_string(M - 1) + ", adjoint after) " : std::string()) + w1;
+      why = (adjoint && !reuse ? "(forward systems 0.." + std::to_string(M - 1) + ", adjoint after) " : std::string()) + w1;
     }
-    RSN_CUDA(c, launch_t_final(ne, n_cols, c->st, q.t_all.as<double>(), q.gr_cols.as<double>(),
-                               q.Td.as<double>() + e0));
-    c->st_launches += 1;
+    if (!reuse) {
+      RSN_CUDA(c, launch_t_final(ne, n_cols, c->st, q.t_all.as<double>(), q.gr_cols.as<double>(),
+                                 q.Td.as<double>() + e0));
+      c->st_launches += 1;
+    }
     if (adjoint) {
       std::vector<double> hw(M);
-      for (long long k = 0; k < M; ++k) hw[k] = 8.0 * c->gr[in.col[k]] * T_bar[e0 + k / n_cols];
+      for (long long k = 0; k < M; ++k) hw[k] = 8.0 * c->gr[cols[k % n_cols]] * T_bar[e0 + k / n_cols];
       RSN_CUDA(c, q.wt.ensure(M * sizeof(double)));
       RSN_CUDA(c, cudaMemcpyAsync(q.wt.p, hw.data(), M * sizeof(double), cudaMemcpyHostToDevice, c->st));
-      RSN_CUDA(c, launch_grad_sys((int)M, N, c->st, X + M * N, X, q.wt.as<double>(), q.g.as<double>()));
+      const double2* xfwd = reuse ? x_given + (size_t)e0 * n_cols * N : X;
+      RSN_CUDA(c, launch_grad_sys((int)M, N, c->st, X + F0 * N, xfwd, q.wt.as<double>(), q.g.as<double>()));
       c->st_launches += 1;
       RSN_CUDA(c, cudaStreamSynchronize(c->st));  // hw lives on the host stack
     }
   }
   RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
-  if (T && n_e > 0) {
+  if (T && n_e > 0 && !reuse) {
     if (n_cols == 0) RSN_CUDA(c, cudaMemsetAsync(q.Td.p, 0, n_e * sizeof(double), c->st));
     RSN_CUDA(c, cudaMemcpyAsync(T, q.Td.p, n_e * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   }
@@ -1410,6 +1527,165 @@ rsn_status rsn_transmission_vjp(rsn_ctx* c, int n_e, const double* E, int n_cols
   if (!c) return RSN_EINVAL;
   if (!dV) RSN_FAIL(c, RSN_EINVAL, "dV is NULL");
   return transmission_impl(c, n_e, E, n_cols, cols, o, T_bar, dV, dV_is_device, T);
+}
+
+}  // extern "C"
+
+// Shared driver of the shifted entry points: one seed system per column at
+// the energy nearest the middle of the window; every energy is a shift of it.
+// Shifts that did not converge within max_iter seed iterations are solved
+// again one by one by the plain FP64 path.  full: every grid point tracked,
+// iterates written to x_dev [n_e][n_cols][N]; else the Gamma_L support only
+// and T[e] = 4 sum_c Gamma_R,c t_{e,c}.
+static rsn_status shifted_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols,
+                               const rsn_solver_opts* o, void* x_dev, int32_t* iters, double* relres, double* T) {
+  rsn_status rs = commit_setup(c);
+  if (rs != RSN_OK) return rs;
+  if ((rs = check_solve_args(c, n_e, E, n_cols, cols, o)) != RSN_OK) return rs;
+  if (o->precision != RSN_FP64)
+    RSN_FAIL(c, RSN_EINVAL, "shifted solves run in FP64: the mixed mode's true-residual replacements would break "
+                            "the collinearity of the shifted residuals");
+  const bool full = x_dev != nullptr;
+  const long long nsys = n_cols;
+  if (n_e == 0 || n_cols == 0) {
+    if (T) for (int e = 0; e < n_e; ++e) T[e] = 0.0;
+    return RSN_OK;
+  }
+  if (!full && c->nL == 0) RSN_FAIL(c, RSN_EINVAL, "Gamma_L is zero everywhere: no transmission to track");
+  if ((rs = enter(c)) != RSN_OK) return rs;
+  reset_stats(c);
+  CallBufs& q = c->cb;
+  const long long N = c->N;
+  const auto t_start = std::chrono::steady_clock::now();
+  RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
+  // seed: the energy nearest the middle of the window
+  double lo = E[0], hi = E[0];
+  for (int e = 1; e < n_e; ++e) lo = std::min(lo, E[e]), hi = std::max(hi, E[e]);
+  int seed = 0;
+  for (int e = 1; e < n_e; ++e)
+    if (std::fabs(E[e] - 0.5 * (lo + hi)) < std::fabs(E[seed] - 0.5 * (lo + hi))) seed = e;
+  ShiftSpec sh;
+  sh.n_shift = n_e;
+  sh.sig.resize(n_e);
+  for (int e = 0; e < n_e; ++e) sh.sig[e] = E[e] - E[seed];
+  sh.n_cols = n_cols;
+  if (full) {
+    std::vector<int> all(N);
+    for (long long i = 0; i < N; ++i) all[i] = (int)i;
+    RSN_CUDA(c, q.sh_idx.ensure(N * sizeof(int)));
+    RSN_CUDA(c, cudaMemcpyAsync(q.sh_idx.p, all.data(), N * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    RSN_CUDA(c, cudaStreamSynchronize(c->st));  // `all` lives on the host stack
+    sh.idx = q.sh_idx.as<int>();
+    sh.nT = (int)N;
+    sh.xs_out = reinterpret_cast<double2*>(x_dev);
+  } else {
+    sh.idx = c->L_idx.as<int>();
+    sh.nT = c->nL;
+  }
+  StreamIn in;
+  in.resize(nsys);
+  for (long long k = 0; k < nsys; ++k) {
+    in.E[k] = E[seed];
+    in.col[k] = cols[k];
+    in.xo[k] = -1;  // the seed's own iterate stays in slot storage
+  }
+  StreamOut so;
+  if ((rs = run_stream(c, o, in, nullptr, nullptr, false, 0, t_start, so, &sh)) != RSN_OK) return rs;
+  const size_t ne_c = (size_t)n_e * n_cols;
+  std::vector<int> sit(ne_c);
+  std::vector<double> srel(ne_c);
+  RSN_CUDA(c, cudaMemcpyAsync(sit.data(), q.sh_sit.p, ne_c * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  RSN_CUDA(c, cudaMemcpyAsync(srel.data(), q.sh_srel.p, ne_c * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  RSN_CUDA(c, q.t_all.ensure(ne_c * sizeof(double)));
+  RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, q.sh_ts.p, ne_c * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  RSN_CUDA(c, cudaStreamSynchronize(c->st));
+  // shifts that missed the tolerance: the plain FP64 path, one system each
+  std::vector<long long> F;
+  StreamIn sub;
+  for (size_t k = 0; k < ne_c; ++k)
+    if (sit[k] < 0) {
+      F.push_back((long long)k);
+      sub.E.push_back(E[k / n_cols]);
+      sub.col.push_back(cols[k % n_cols]);
+      sub.junc.push_back(0);
+      sub.dep.push_back(-1);
+      sub.bn2.push_back(0.0);
+      sub.xo.push_back(full ? (long long)k * N : -1);
+      sub.xfo.push_back(0);
+    }
+  std::string why;
+  rsn_status worst = RSN_OK;
+  if (!F.empty()) {
+    StreamOut s2;
+    if ((rs = run_stream(c, o, sub, full ? reinterpret_cast<double2*>(x_dev) : nullptr, nullptr, !full, 0, t_start,
+                         s2)) != RSN_OK)
+      return rs;
+    for (size_t f = 0; f < F.size(); ++f) {
+      sit[F[f]] = s2.status[f] == 0 ? -1000000 - s2.iters[f] : -std::max(1, s2.iters[f]);
+      srel[F[f]] = s2.relres[f];
+      if (!full)
+        RSN_CUDA(c, cudaMemcpyAsync(q.t_all.as<double>() + F[f], q.out_t.as<double>() + f, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->st));
+    }
+    c->st_fallback += (int64_t)F.size();
+    worst = stream_status(s2, 0, (long long)F.size(), nullptr, nullptr, &why);
+  }
+  if (iters)
+    for (size_t k = 0; k < ne_c; ++k)
+      iters[k] = sit[k] >= 0 ? sit[k] : (sit[k] <= -1000000 ? -1000000 - sit[k] : sit[k]);
+  if (relres)
+    for (size_t k = 0; k < ne_c; ++k) relres[k] = srel[k];
+  if (T) {
+    RSN_CUDA(c, q.gr_cols.ensure(n_cols * sizeof(double)));
+    RSN_CUDA(c, q.Td.ensure(n_e * sizeof(double)));
+    std::vector<double> hgr(n_cols);
+    for (int k = 0; k < n_cols; ++k) hgr[k] = c->gr[cols[k]];
+    RSN_CUDA(c, cudaMemcpyAsync(q.gr_cols.p, hgr.data(), n_cols * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    RSN_CUDA(c, launch_t_final(n_e, n_cols, c->st, q.t_all.as<double>(), q.gr_cols.as<double>(), q.Td.as<double>()));
+    RSN_CUDA(c, cudaMemcpyAsync(T, q.Td.p, n_e * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  }
+  RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
+  RSN_CUDA(c, cudaStreamSynchronize(c->st));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->t0, c->t1);
+  c->st_ms = ms;
+  if ((rs = leave(c)) != RSN_OK) return rs;
+  if (worst != RSN_OK) RSN_FAIL(c, worst, "some shifted systems did not reach tol in the FP64 re-solve: %s", why.c_str());
+  return RSN_OK;
+}
+
+extern "C" {
+
+rsn_status rsn_solve_columns_shifted(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols,
+                                     const rsn_solver_opts* o, void* x_dev, int32_t* iters, double* relres) {
+  if (!c) return RSN_EINVAL;
+  if ((long long)n_e * n_cols > 0 && !x_dev) RSN_FAIL(c, RSN_EINVAL, "x_dev is NULL");
+  return shifted_impl(c, n_e, E, n_cols, cols, o, x_dev, iters, relres, nullptr);
+}
+
+rsn_status rsn_transmission_shifted(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols,
+                                    const rsn_solver_opts* o, double* T, int32_t* iters) {
+  if (!c) return RSN_EINVAL;
+  if (n_e > 0 && !T) RSN_FAIL(c, RSN_EINVAL, "T is NULL");
+  return shifted_impl(c, n_e, E, n_cols, cols, o, nullptr, iters, nullptr, T);
+}
+
+rsn_status rsn_transmission_keep(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols,
+                                 const rsn_solver_opts* o, void* x_dev, double* T) {
+  if (!c) return RSN_EINVAL;
+  if (n_e > 0 && !T) RSN_FAIL(c, RSN_EINVAL, "T is NULL");
+  if ((long long)n_e * n_cols > 0 && !x_dev) RSN_FAIL(c, RSN_EINVAL, "x_dev is NULL");
+  return transmission_impl(c, n_e, E, n_cols, cols, o, nullptr, nullptr, 0, T, reinterpret_cast<double2*>(x_dev));
+}
+
+rsn_status rsn_transmission_vjp_reuse(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols,
+                                      const rsn_solver_opts* o, const void* x_dev, const double* T_bar, double* dV,
+                                      int dV_is_device) {
+  if (!c) return RSN_EINVAL;
+  if (!dV) RSN_FAIL(c, RSN_EINVAL, "dV is NULL");
+  if ((long long)n_e * n_cols > 0 && !x_dev) RSN_FAIL(c, RSN_EINVAL, "x_dev is NULL");
+  return transmission_impl(c, n_e, E, n_cols, cols, o, T_bar, dV, dV_is_device, nullptr, nullptr,
+                           reinterpret_cast<const double2*>(x_dev));
 }
 
 rsn_status rsn_batch_transmission(int n_ctx, rsn_ctx* const* ctxs, const int* n_e, const double* const* E,
@@ -1586,7 +1862,8 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
     const int lz = (c->nz + zt - 1) / zt;
     if (lz >= 2 * c->R + 2 || zt == 1) lzs.push_back(lz);
   }
-  for (int lz : lzs) cands.push_back({0, lz, 0, 0});   // FP32 point-pair kernel where it applies
+  for (int lz : lzs) cands.push_back({0, lz, 0, -2});  // FP32 point-pair kernel where it applies
+  for (int lz : lzs) cands.push_back({0, lz, 0, -3});  // FP32 plane kernel where it applies
   for (int lz : lzs) cands.push_back({0, lz, 0, -1});  // whole-plane bulk-copy kernel
   for (int p = 1; p <= 4; ++p)
     for (int ty : {c->ny, (c->ny + 1) / 2, (c->ny + 2) / 3})
@@ -1628,7 +1905,10 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
   if (TY) *TY = bestc.TY;
   if (Lz) *Lz = bestc.Lz;
   if (ppt) *ppt = bestc.ppt;
-  if (tma) *tma = bestc.notma == -1 ? 1 : (bestc.TY == 0 && bestc.ppt == 0 ? 2 : 0);
+  if (tma) {
+    const Tiling tb = choose_tiling(c, !fp32, OP_COCG, nslots);
+    *tma = tb.plane ? 3 : tb.pair ? 2 : tb.tma ? 1 : 0;
+  }
   if (best_gbs) *best_gbs = best;
   (void)fp32;
   return leave(c);
@@ -1637,11 +1917,11 @@ rsn_status rsn_autotune(rsn_ctx* c, int precision, int nslots, int* TY, int* Lz,
 // Tiling override used by the autotuner and the tests: TY, Lz, ppt (0 = auto).
 rsn_status rsn_set_tiling(rsn_ctx* c, int TY, int Lz, int ppt) {
   if (!c) return RSN_EINVAL;
-  if (TY < 0 || Lz < 0 || ppt < -1 || ppt > 4) RSN_FAIL(c, RSN_EINVAL, "bad tiling override");
+  if (TY < 0 || Lz < 0 || ppt < -3 || ppt > 4) RSN_FAIL(c, RSN_EINVAL, "bad tiling override");
   c->tile_override[0] = TY;
   c->tile_override[1] = Lz;
   c->tile_override[2] = ppt > 0 ? ppt : 0;
-  c->tile_override[3] = ppt == -1 ? -1 : 0;
+  c->tile_override[3] = ppt < 0 ? ppt : 0;
   clear_graphs(c);
   c->ws.generation++;
   c->ws.slots = 0;  // partial strides may change

@@ -23,7 +23,8 @@ constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
 // by the zero-padded tail of an atom's last value quad
 constexpr int kCePad = 16;
 constexpr int kMaxGraphIters = 256;
-constexpr int kMaxApplyRhs = 65535;  // vectors per operator-application call (grid y dimension)
+constexpr int kMaxApplyRhs = 65535;
+constexpr int kMaxGoalChecks = 24;   // true residuals of a goal phase before its iterate is kept  // vectors per operator-application call (grid y dimension)
 constexpr int kSchedThreads = 1024;
 // CTA rows of the kernels that work only on NEW / CHECK slots (zero, true
 // residual and its projections, x update): each row takes list entries
@@ -79,7 +80,9 @@ enum SlotState {
   SL_NEW = 1,     // system assigned: zero x and d, then true residual r = b
   SL_CHECK = 2,   // recurrence reached its target: FP64 true residual + reliable update
   SL_ACTIVE = 3,  // COCG iterations in the inner precision
-  SL_DRAIN = 4    // finished this iteration: outputs are emitted, then FREE
+  SL_DRAIN = 4,   // finished this iteration: outputs are emitted, then FREE
+  SL_CHECKT = 5   // goal phase: the recurrence reached its next target; x += sigma d and the
+                  // T partial of x are taken without touching the recurrence (no true residual)
 };
 
 // Batch state.  Lives in device memory; kernels receive a pointer to it so
@@ -121,6 +124,12 @@ struct BatchDev {
   // reduction partials
   double2* rho0_part;   // [S][PA] true-residual kernel: r^T r
   double* nrm0_part;    // [S][PA] true-residual kernel: ||r||^2
+  double* t0_part;      // [S][PA] true-residual kernel: sum Gamma_L |x|^2 of the iterate (forward systems)
+  double* tlast;        // [S] that sum at the previous true residual (-1: none yet)
+  int* gcnt;            // [S] T checks since the residual met tol (goal phase)
+  int* gphase;          // [S] 1: goal phase (the residual met tol, the T partial is converging)
+  double* tgoal;        // [S] T partial of x at a goal-phase check
+  double* rgoal;        // [S] relative true residual when the goal phase began
   double2* rho_part;    // [S][PB] COCG update kernel: r^T r
   double* nrm_part;     // [S][PB]
   double2* mu_part;     // [S][PA] operator kernel: p^T A p
@@ -150,9 +159,30 @@ struct BatchDev {
   int* fslot;                // FREE slots in slot order (scheduler scratch)
   void* c_e;                 // e_kb[p] c_p[p] of the current direction per slot (inner precision),
   int ce_stride;             // n_proj + kCePad entries per slot, the last kCePad always zero
+  // shifted systems: one seed Krylov space per column serves every energy of a
+  // window, A(E_e) = A(E_seed) + sigma_e 1 (Eq. G); n_shift = 0 for plain solves
+  int n_shift;
+  const double* shift_sig;   // sigma_e = E_e - E_seed, e < n_shift
+  int nT;                    // tracked points of the shifted iterates
+  const int* T_idx;          // their grid indices (the Gamma_L support, or every point)
+  double2* xs;               // shifted iterates x_e on the tracked points
+  long long xs_sstride;      // xs offset of slot / system k: k * xs_sstride + e * xs_estride
+  long long xs_estride;
+  int xs_by_sys;             // 1: xs is indexed by system (caller's output), 0: by slot
+  double2* ps;               // shifted directions p_e: [slot][n_shift][nT]
+  double2* spi;              // pi_{e,k} ring: [3][slot][n_shift], iteration k in ring k % 3
+  int* sconv_it;             // [slot][n_shift] iteration at which shift e converged (INT_MAX: not yet)
+  double2* salpha;           // [2][slot] alpha_k of the seed recurrence, ring k % 2
+  double2* sbeta;            // [2][slot] beta_k, ring k % 2
+  double* rn2;               // [slot] ||r_{k+1}||^2 of the seed (bookkeeping kernel)
+  double* out_ts;            // [n_shift][system] T partial sum_{i in L} Gamma_L |x_e(i)|^2
+  int* out_sit;              // [n_shift][system] seed iterations at convergence (-1: not converged)
+  double* out_srel;          // [n_shift][system] recurrence estimate ||r_k|| / |pi_{e,k}| / ||b||
   // options
   double tol, delta;
   double tol_adj;  // tolerance of systems with a computed right-hand side (col < 0)
+  double tol_T;    // forward systems also finish only once sum Gamma_L |x|^2 changed by at most
+                   // tol_T of itself between two true residuals (0: residual criterion alone)
   int max_iter, max_upd;
   int cycle_cap;  // a cycle longer than this ends with a true residual even if its target was not met
   int stall_cap;  // true residuals in a row without a 4x gain before a system is handed back (0 = never)
@@ -176,10 +206,15 @@ size_t op_tma_smem_bytes(bool fp32, int mode, int R, int nx, int ny, int n_proj)
 constexpr int kPairThreads = 288;     // threads per CTA of the two-CTAs-per-SM variant
 constexpr int kPairThreadsBig = 640;  // one CTA per SM (planes of up to 1280 points)
 constexpr int kPairStages = 4;        // input planes in flight per CTA
+constexpr int kPlaneThreads = 576;    // one-point-per-thread plane kernel: threads per CTA (two per SM)
 constexpr int kPairXO = 8;            // zero columns left of x = 0 in the exchange tile (>= R, even)
 cudaError_t launch_op_pair(int mode, int R, bool big, dim3 grid, int threads, size_t smem, cudaStream_t st,
                            const JuncDev* jt, const BatchDev* b, const void* x_in, void* y_out, const void* c_in);
 size_t op_pair_smem_bytes(int mode, int R, int nx, int ny, int n_proj);
+// FP32 one-point-per-thread kernel with plane streaming: whole planes of an
+// even number of at most kPlaneThreads points; same shared-memory layout
+cudaError_t launch_op_plane(int mode, int R, dim3 grid, int threads, size_t smem, cudaStream_t st, const JuncDev* jt,
+                            const BatchDev* b, const void* x_in, void* y_out, const void* c_in);
 
 cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
@@ -193,9 +228,16 @@ cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, cons
                             const BatchDev* b);
 cudaError_t launch_emit(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_list(cudaStream_t st, const BatchDev* b);
+cudaError_t launch_tgoal(cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_qproj(bool fp32, int nslots, int nS, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_t_final(int n_e, int n_cols, cudaStream_t st, const double* t_all,
                            const double* gr_cols, double* T_out);
+// shifted systems: initialisation of NEW slots, the per-iteration update of
+// the shifted iterates (after the bookkeeping kernel) and their T partials
+cudaError_t launch_shift_init(int nT, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
+cudaError_t launch_shift_update(int nslots, int nT, int n_shift, cudaStream_t st, const JuncDev* jt,
+                                const BatchDev* b);
+cudaError_t launch_shift_emit(int nslots, int n_shift, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_grad_sys(int nsys, long long N, cudaStream_t st, const double2* lam, const double2* x,
                             const double* wt, double* g);
 

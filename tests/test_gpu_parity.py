@@ -44,7 +44,7 @@ JUNCTIONS = {
 
 
 @pytest.mark.parametrize("name", sorted(JUNCTIONS))
-@pytest.mark.parametrize("tiling", [(0, 0, 0), (5, 7, 2), (3, 9, 1), (0, 11, -1)])
+@pytest.mark.parametrize("tiling", [(0, 0, 0), (5, 7, 2), (3, 9, 1), (0, 11, -1), (0, 13, -2), (0, 17, -3)])
 def test_apply_matches_oracle_operator(B, name, tiling):
     j = JUNCTIONS[name]()
     ctx = B.Context(0).set_junction(j)
@@ -151,6 +151,27 @@ def test_vjp_matches_oracle_gradient(B, prec):
     else:
         assert np.all(np.abs(T - T_ref) <= 1e-6)
         assert np.abs(g - g_ref).max() <= 1e-5 * gs
+    ctx.close()
+
+
+@pytest.mark.parametrize("tiling", [(0, 0, 0), (0, 13, -2), (0, 17, -3), (0, 11, -1), (4, 6, 2), "autotune"])
+def test_mixed_solves_under_every_operator_kernel(B, tiling):
+    # the COCG operator of the mixed solver: automatic (point-pair), point-pair,
+    # plane kernel, whole-plane bulk-copy with a shifted queue, register kernel,
+    # the autotuner's pick
+    j = JUNCTIONS["junction_R4"]()
+    E = [0.19]
+    cols = j.right_columns()[::53]
+    ctx = B.Context(0).set_junction(j)
+    if tiling == "autotune":
+        pick = ctx.autotune(B.RSN_MIXED, 64)
+        assert pick["gbs"] > 0 and pick["tma"] in (0, 1, 2, 3)
+    else:
+        ctx.set_tiling(*tiling)
+    x, iters, relres = ctx.solve_columns(E, cols, B.default_opts(B.RSN_MIXED))
+    ref = O.solve_columns(j, E[0], cols).T
+    err = np.linalg.norm(x[0].cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 1e-6 and relres.max() <= 1e-10, (err.max(), relres.max())
     ctx.close()
 
 
