@@ -452,6 +452,55 @@ def run_ours(args):
                     "construction; rel_dT is the meaningful figure",
         }
 
+    # ---- an energy window by shifted COCG against one solve per energy ----
+    if rank == 0 and not args.no_fp64 and args.window_energies > 0:
+        E_win = np.linspace(E_LO, E_HI, args.window_energies)
+        wcols = all_cols[:: max(1, all_cols.size // args.window_cols)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ts, its = ctx.transmission_shifted(E_win, wcols, B.default_opts(B.RSN_FP64), return_iters=True)
+        ts = time.perf_counter() - t0
+        ss = ctx.last_stats()
+        t0 = time.perf_counter()
+        Tm = ctx.transmission(E_win, wcols, B.default_opts(B.RSN_MIXED))
+        tm = time.perf_counter() - t0
+        sm = ctx.last_stats()
+        n = E_win.size * wcols.size
+        result["window_T"] = {
+            "sample": f"{wcols.size} right-CAP columns x {E_win.size} energies linspace({E_LO},{E_HI}); host-timed",
+            "shifted_fp64_solves_per_s": n / ts, "per_energy_mixed_solves_per_s": n / tm,
+            "shifted_over_mixed": tm / ts,
+            "seed_iterations_max": int(its.max()), "operator_applications_shifted": ss["krylov_iters"],
+            "operator_applications_per_energy_mixed": sm["krylov_iters"],
+            "max_rel_dT_shifted_vs_mixed": float(np.max(np.abs(Ts - Tm) / np.abs(Ts))),
+            "plain_fp64_fallbacks": ss["fp64_fallbacks"],
+        }
+
+    # ---- many uneven junctions in one slot pool ----------------------------
+    if rank == 0 and args.batch_junctions > 0:
+        bj = P.batched_junctions()[: args.batch_junctions]
+        bctx = [B.Context(local).set_junction(x) for x in bj]
+        bE = [np.linspace(0.16, 0.24, args.batch_energies) for _ in bj]
+        bcols = [x.right_columns()[:: args.batch_col_stride] for x in bj]
+        ob = B.default_opts(B.RSN_MIXED, deadline_ms=args.deadline * 1e3)
+        B.batch_transmission(bctx[:2], bE[:2], bcols[:2], ob)  # untimed warm-up (pool set-up, kernels loaded)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.batch_transmission(bctx, bE, bcols, ob)
+        tb = time.perf_counter() - t0
+        sb = bctx[0].last_stats()
+        nb = sum(e.size * c.size for e, c in zip(bE, bcols))
+        result["batched_junctions"] = {
+            "sample": f"{len(bj)} seeded uneven junctions (cross-sections 12..32, 64..192 planes, CAP 6..10, "
+                      f"5..30 wells), {args.batch_energies} energies in [0.16, 0.24] Ha each, every "
+                      f"{args.batch_col_stride}th right-CAP column: {nb} forward solves in one slot pool, mixed "
+                      "precision; host-timed library call",
+            "columns_per_s": nb / tb, "seconds": tb, "krylov_iters_per_solve": sb["krylov_iters"] / nb,
+            "fp64_fallbacks": sb["fp64_fallbacks"],
+        }
+        for x in bctx:
+            x.close()
+
     # ---- parity against the oracle's golden columns ------------------------
     if rank == 0 and not args.no_fp64:
         gold = load_golden()
@@ -542,7 +591,12 @@ def main():
     ap.add_argument("--roofline-steps", type=int, default=2, help="steps of the event-timed roofline pass")
     ap.add_argument("--fwd-energies", type=int, default=2, help="energies of the forward-T comparison")
     ap.add_argument("--fwd-cols", type=int, default=0, help="columns of the forward-T comparison (0 = all 4,608)")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the forward-T and parity legs")
+    ap.add_argument("--window-energies", type=int, default=16, help="energies of the shifted-COCG window leg (0 = skip)")
+    ap.add_argument("--window-cols", type=int, default=128, help="columns of the shifted-COCG window leg")
+    ap.add_argument("--batch-junctions", type=int, default=64, help="junctions of the slot-pool leg (0 = skip)")
+    ap.add_argument("--batch-energies", type=int, default=8, help="energies per junction in the slot-pool leg")
+    ap.add_argument("--batch-col-stride", type=int, default=256, help="every k-th right-CAP column in the pool leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the forward-T, window and parity legs")
     ap.add_argument("--deadline", type=float, default=240.0, help="seconds allowed per library call")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

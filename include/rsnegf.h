@@ -240,10 +240,16 @@ rsn_status rsn_transmission_vjp_reuse(rsn_ctx* ctx, int n_e, const double* E, in
    of uneven sizes; each junction is Eq. T-realspace on its own context):
    ctxs[k] holds junction k (distinct contexts, all set up); it gets n_e[k]
    energies E[k] and n_cols[k] columns cols[k], and T[k] (host, n_e[k] doubles)
-   receives its T as rsn_transmission would.  Each context solves on its own
-   stream from its own host thread, so the junctions share the GPU through
-   concurrent streams; when opts->rhs_block is 0, each context's slot pool is
-   capped by its share of the free device memory.  opts may be NULL (RSN_MIXED
+   receives its T as rsn_transmission would.  When every context is on the same
+   device with the same FD order and opts->rhs_block is 0, all (junction,
+   energy, column) systems wait in ONE queue of one slot pool owned by ctxs[0]
+   (its stream, slots and captured graphs): each slot works on its system's
+   junction with that junction's tiling, and every launch of the solver serves
+   all junctions; junctions whose planes need different operator kernels run
+   them side by side.  The pool runs all junctions or none: if any junction's
+   arguments are refused, every junction reports RSN_EINVAL.  Otherwise each
+   context solves on its own stream from its own host thread (its slot pool
+   capped by its share of the free device memory).  opts may be NULL (RSN_MIXED
    defaults).  status (n_ctx entries, may be NULL) receives each junction's
    result; the call returns RSN_OK if all succeeded, else the first failing
    junction's status (its message is in rsn_last_error(ctxs[k])).

@@ -112,7 +112,7 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
   }
   const JuncDev& J = jt[b.junc[s]];
   const int tile = blockIdx.x;
-  if (tile >= J.nA) return;
+  if (tile >= J.nA || (MODE != OP_RESID && J.kind != kOpReg)) return;
 
   const int nx = J.nx, ny = J.ny, nz = J.nz, plane = J.plane, TY = J.TY;
   const int yt = tile % J.ytiles, zt = tile / J.ytiles;
@@ -153,13 +153,13 @@ __device__ __forceinline__ void op_tile(const JuncDev* __restrict__ jt, const Ba
   const int n_proj = J.n_proj;
   if (MODE != OP_COCG && n_proj > 0) {
     if constexpr (MODE == OP_RESID) {
-      const double2* cxp = b.c_x + (size_t)s * n_proj;
+      const double2* cxp = b.c_x + (size_t)s * b.pstride;
       for (int p = tid; p < n_proj; p += nt) {
         const double e = J.ekb[p];
         ce[p] = mk2((CT)(e * cxp[p].x), (CT)(e * cxp[p].y));
       }
     } else {
-      const CO* cin = reinterpret_cast<const CO*>(c_in) + (size_t)s * n_proj;
+      const CO* cin = reinterpret_cast<const CO*>(c_in) + (size_t)s * b.pstride;
       for (int p = tid; p < n_proj; p += nt) {
         const CT e = (CT)J.ekb[p];
         C c = cin[p];
@@ -454,7 +454,7 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
   }
   const JuncDev& J = jt[b.junc[s]];
   const int tile = blockIdx.x;
-  if (tile >= J.nA) return;
+  if (tile >= J.nA || J.kind != kOpTma) return;
   const int nx = J.nx, ny = J.ny, nz = J.nz, plane = J.plane;
   const int z0 = tile * J.Lz, z1 = min(z0 + J.Lz, nz);
   const int pitch = nx + 2 * R, prow = ny + 2 * R;
@@ -494,7 +494,7 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
   }
   // APPLY only: in COCG the projector term of q is added on the support points
   if (MODE != OP_COCG && n_proj > 0) {
-    const C* cin = reinterpret_cast<const C*>(c_in) + (size_t)s * n_proj;
+    const C* cin = reinterpret_cast<const C*>(c_in) + (size_t)s * b.pstride;
     for (int p = tid; p < n_proj; p += nt) {
       const T e = (T)J.ekb[p];
       const C c = cin[p];

@@ -83,7 +83,7 @@ op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, 
   }
   const JuncDev& J = jt[b.junc[s]];
   const int tile = blockIdx.x;
-  if (tile >= J.nA) return;
+  if (tile >= J.nA || J.kind != kOpPair) return;
 
   const int nx = J.nx, ny = J.ny, nz = J.nz, plane = J.plane;
   const int hx = nx >> 1;  // pairs per row
@@ -129,7 +129,7 @@ op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, 
     yv = reinterpret_cast<float2*>(y_out) + vo;
   }
   if (MODE == OP_APPLY && n_proj > 0) {
-    const float2* cin = reinterpret_cast<const float2*>(c_in) + (size_t)s * n_proj;
+    const float2* cin = reinterpret_cast<const float2*>(c_in) + (size_t)s * b.pstride;
     for (int p = tid; p < n_proj; p += nt) {
       const float e = (float)J.ekb[p];
       const float2 c = cin[p];
@@ -340,7 +340,7 @@ op_plane_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp,
   }
   const JuncDev& J = jt[b.junc[s]];
   const int tile = blockIdx.x;
-  if (tile >= J.nA) return;
+  if (tile >= J.nA || J.kind != kOpPlane) return;
 
   const int nx = J.nx, ny = J.ny, nz = J.nz, plane = J.plane;
   const int z0 = tile * J.Lz, z1 = min(z0 + J.Lz, nz);
@@ -392,7 +392,7 @@ op_plane_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp,
     yv = reinterpret_cast<float2*>(y_out) + vo;
   }
   if (MODE == OP_APPLY && n_proj > 0) {
-    const float2* cin = reinterpret_cast<const float2*>(c_in) + (size_t)s * n_proj;
+    const float2* cin = reinterpret_cast<const float2*>(c_in) + (size_t)s * b.pstride;
     for (int p = tid; p < n_proj; p += nt) {
       const float e = (float)J.ekb[p];
       const float2 c = cin[p];

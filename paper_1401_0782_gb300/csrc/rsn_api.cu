@@ -99,6 +99,20 @@ struct ShiftSpec {
   long long n_cols = 0;
 };
 
+// A slot pool over several junctions of one device (rsn_batch_transmission):
+// the per-junction operator data stay with their contexts; one JuncDev per
+// junction carries its tilings, and each slot works on its system's junction.
+struct PoolSpec {
+  int K = 0, R = 0;
+  long long N = 0;  // the largest junction: slot vectors are this long
+  int n_proj = 0, n_groups = 0, max_np = 1, nB = 0, nS = 0, PA = 0, PB = 0;
+  Tiling inner[4];                        // launch configuration per operator kind (OpKind)
+  bool has[4] = {false, false, false, false};
+  Tiling resid;                           // launch configuration of the true-residual kernel
+  const JuncDev* ji = nullptr;            // device: K JuncDev with the COCG tilings
+  const JuncDev* jr = nullptr;            // device: K JuncDev with the residual tilings
+};
+
 struct GraphKey {
   int fp32, slots, iters, generation, proj, timing, n_shift, nT;
   bool operator<(const GraphKey& o) const {
@@ -134,6 +148,7 @@ struct rsn_ctx {
   int n_groups = 0, nL = 0, max_np = 1;
   JuncDev jh{};
   DevBuf jd;  // device JuncDev (one per launch configuration, uploaded before a batch)
+  DevBuf pool_jd;  // device JuncDev of a slot pool over several junctions (this context owns the pool)
 
   Workspace ws;
   CallBufs cb;
@@ -490,6 +505,7 @@ static rsn_status make_cfg(rsn_ctx* c, const Tiling& inner, const Tiling& resid,
     js[k].ztiles = t.ztiles;
     js[k].nA = t.n;
     js[k].nR = cfg.resid.n;
+    js[k].kind = k == 1 ? kOpReg : t.plane ? kOpPlane : t.pair ? kOpPair : t.tma ? kOpTma : kOpReg;
   }
   RSN_CUDA(c, cudaMemcpyAsync(c->jd.p, js, 2 * sizeof(JuncDev), cudaMemcpyHostToDevice, c->st));
   cfg.jt_inner = c->jd.as<JuncDev>();
@@ -716,12 +732,14 @@ static size_t slot_bytes(const rsn_ctx* c, bool fp32) {
 // Slots: enough systems in flight to fill the GPU, few enough (relative to the
 // queue) that the drain at the end of the queue stays short, and within memory.
 static int choose_slots(rsn_ctx* c, const rsn_solver_opts* o, long long nsys, size_t reserved,
-                        size_t extra_per_slot = 0) {
+                        size_t extra_per_slot = 0, long long N_pool = 0) {
   if (o->rhs_block > 0) return (int)std::max<long long>(1, std::min<long long>(o->rhs_block, nsys));
   size_t fr = 0, tot = 0;
   cudaMemGetInfo(&fr, &tot);
   const double avail = fr > reserved ? 0.6 * (double)(fr - reserved) : 0.0;
-  long long cap = (long long)(avail / (double)(slot_bytes(c, o->precision == RSN_MIXED) + extra_per_slot));
+  const size_t per_slot = N_pool > 0 ? slot_bytes(c, o->precision == RSN_MIXED) * (size_t)N_pool / (size_t)c->N
+                                     : slot_bytes(c, o->precision == RSN_MIXED);
+  long long cap = (long long)(avail / (double)(per_slot + extra_per_slot));
   cap = std::max<long long>(1, std::min<long long>(cap, 8192));
   // one slot per system up to 2048: a stream then ends with its slowest
   // system instead of with a second wave of systems that waited for slots
@@ -729,13 +747,21 @@ static int choose_slots(rsn_ctx* c, const rsn_solver_opts* o, long long nsys, si
   return (int)std::max<long long>(1, std::min(want, cap));
 }
 
-static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
+static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S, const PoolSpec* pool = nullptr) {
   Workspace& w = c->ws;
-  const long long N = c->N;
-  const Tiling ti = choose_tiling(c, !fp32, OP_COCG, S), tr = choose_tiling(c, true, OP_RESID, S);
-  // mu partials: the operator tiles', then one per atom (projection kernel)
-  const int PA = std::max(ti.n + c->n_groups, tr.n), PB = c->jh.nB;
-  if (w.slots == S && w.fp32 == fp32 && w.N == N && w.PA == PA && w.PB == PB && w.n_proj == c->n_proj)
+  const long long N = pool ? pool->N : c->N;
+  const int n_proj = pool ? pool->n_proj : c->n_proj;
+  int PA, PB;
+  if (pool) {
+    PA = pool->PA;
+    PB = pool->PB;
+  } else {
+    const Tiling ti = choose_tiling(c, !fp32, OP_COCG, S), tr = choose_tiling(c, true, OP_RESID, S);
+    // mu partials: the operator tiles', then one per atom (projection kernel)
+    PA = std::max(ti.n + c->n_groups, tr.n);
+    PB = c->jh.nB;
+  }
+  if (w.slots == S && w.fp32 == fp32 && w.N == N && w.PA == PA && w.PB == PB && w.n_proj == n_proj)
     return RSN_OK;
   const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
   const size_t vb = (size_t)S * N;
@@ -779,7 +805,7 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   RSN_CUDA(c, w.mu.ensure((size_t)S * PA * sizeof(double2)));
   RSN_CUDA(c, w.rho.ensure((size_t)S * PB * sizeof(double2)));
   RSN_CUDA(c, w.nrm.ensure((size_t)S * PB * sizeof(double)));
-  const size_t npj = std::max(1, c->n_proj);
+  const size_t npj = std::max(1, n_proj);
   RSN_CUDA(c, w.c_r.ensure((size_t)S * npj * sizeof(double2)));
   RSN_CUDA(c, w.c_p.ensure(2 * (size_t)S * npj * sizeof(double2)));
   RSN_CUDA(c, w.c_x.ensure((size_t)S * npj * sizeof(double2)));
@@ -799,7 +825,7 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S) {
   w.N = N;
   w.PA = PA;
   w.PB = PB;
-  w.n_proj = c->n_proj;
+  w.n_proj = n_proj;
   w.generation++;
   clear_graphs(c);
   return RSN_OK;
@@ -912,7 +938,8 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.lst_n = w.lst_n.as<int>();
   b.fslot = w.fslot.as<int>();
   b.c_e = w.c_e.p;
-  b.ce_stride = std::max(1, c->n_proj) + kCePad;
+  b.ce_stride = std::max(1, c->ws.n_proj) + kCePad;
+  b.pstride = c->ws.n_proj;
   b.tol = o->tol;
   b.tol_adj = o->tol_adjoint > 0 ? o->tol_adjoint : o->tol;
   b.tol_T = o->tol_T;
@@ -932,19 +959,18 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
 static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamIn& in, double2* x64_base,
                              const double2* xf_base, bool want_t, size_t reserved,
                              std::chrono::steady_clock::time_point t_start, StreamOut& out,
-                             const ShiftSpec* sh = nullptr) {
+                             const ShiftSpec* sh = nullptr, const PoolSpec* pool = nullptr) {
   const long long nsys = (long long)in.E.size();
   const bool fp32 = o->precision == RSN_MIXED;
   const int ns = sh ? sh->n_shift : 0;
   const size_t shift_slot_bytes = sh ? (size_t)ns * sh->nT * sizeof(double2) * (sh->xs_out ? 1 : 2) : 0;
-  const int S = choose_slots(c, o, nsys, reserved, shift_slot_bytes);
-  rsn_status rs = ensure_ws(c, fp32, S);
+  const int S = choose_slots(c, o, nsys, reserved, shift_slot_bytes, pool ? pool->N : 0);
+  rsn_status rs = ensure_ws(c, fp32, S, pool);
   if (rs != RSN_OK) return rs;
   if ((rs = ensure_calls(c, nsys)) != RSN_OK) return rs;
   Workspace& w = c->ws;
   CallBufs& q = c->cb;
   cudaStream_t st = c->st;
-  const long long N = c->N;
   // system queue
   RSN_CUDA(c, cudaMemcpyAsync(q.sys_junc.p, in.junc.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st));
   RSN_CUDA(c, cudaMemcpyAsync(q.sys_E.p, in.E.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1025,11 +1051,32 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
   const BatchDev* bdev = c->bd.as<BatchDev>();
 
   LaunchCfg cfg;
-  if ((rs = make_cfg(c, fp32, S, cfg)) != RSN_OK) return rs;
-  const JuncDev* ji = cfg.jt_inner;
-  const JuncDev* jr = cfg.jt_resid;
-  const int nB = c->jh.nB;
-  const bool proj = c->n_proj > 0;
+  const JuncDev* ji;
+  const JuncDev* jr;
+  int nB, n_groups, max_np, nS, R;
+  bool proj;
+  if (pool) {
+    ji = pool->ji;
+    jr = pool->jr;
+    cfg.resid = pool->resid;
+    nB = pool->nB;
+    proj = pool->n_proj > 0;
+    n_groups = pool->n_groups;
+    max_np = pool->max_np;
+    nS = pool->nS;
+    R = pool->R;
+  } else {
+    if ((rs = make_cfg(c, fp32, S, cfg)) != RSN_OK) return rs;
+    ji = cfg.jt_inner;
+    jr = cfg.jt_resid;
+    nB = c->jh.nB;
+    proj = c->n_proj > 0;
+    n_groups = c->n_groups;
+    max_np = c->max_np;
+    nS = c->jh.nS;
+    R = c->R;
+  }
+  const bool multi = pool && pool->K > 1;
   const int KL = std::min(S, kListRows);
   const bool goal = o->tol_T > 0 && !sh;
   const dim3 gr(cfg.resid.n, KL);
@@ -1048,9 +1095,10 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       if ((e = launch_list(st, bdev)) != cudaSuccess) return e;
       if ((e = launch_zero(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
       if (sh && (e = launch_shift_init(sh->nT, st, jr, bdev)) != cudaSuccess) return e;
-      if (proj && (e = launch_project(1, fp32, KL, c->n_groups, c->max_np, st, jr, bdev, nullptr, w.c_x.p)) != cudaSuccess)
+      if (proj && (e = launch_project(1, fp32, KL, n_groups, max_np, st, jr, bdev, nullptr, w.c_x.p, multi)) !=
+                      cudaSuccess)
         return e;
-      if ((e = launch_op(OP_RESID, fp32, c->R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, bdev,
+      if ((e = launch_op(OP_RESID, fp32, R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, bdev,
                          nullptr, nullptr, nullptr)) != cudaSuccess)
         return e;
       if ((e = launch_x_update(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
@@ -1058,13 +1106,22 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       if ((e = launch_sched(S, it, st, jr, bdev)) != cudaSuccess) return e;
       if ((e = launch_emit(S, st, jr, bdev)) != cudaSuccess) return e;
       if (sh && (e = launch_shift_emit(S, ns, st, jr, bdev)) != cudaSuccess) return e;
-      if (proj && (e = launch_project(0, fp32, S, c->n_groups, c->max_np, st, ji, bdev, nullptr, w.c_r.p)) != cudaSuccess)
+      if (proj && (e = launch_project(0, fp32, S, n_groups, max_np, st, ji, bdev, nullptr, w.c_r.p, multi)) !=
+                      cudaSuccess)
         return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it], st, evf)) != cudaSuccess) return e;
-      e = launch_inner(c, cfg.inner, OP_COCG, fp32, S, st, ji, bdev, nullptr, nullptr, nullptr);
-      if (e != cudaSuccess) return e;
+      if (pool) {
+        for (int kd = 0; kd < 4; ++kd)
+          if (pool->has[kd] &&
+              (e = launch_inner(c, pool->inner[kd], OP_COCG, fp32, S, st, ji, bdev, nullptr, nullptr, nullptr)) !=
+                  cudaSuccess)
+            return e;
+      } else if ((e = launch_inner(c, cfg.inner, OP_COCG, fp32, S, st, ji, bdev, nullptr, nullptr, nullptr)) !=
+                 cudaSuccess) {
+        return e;
+      }
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 1], st, evf)) != cudaSuccess) return e;
-      if (proj && (e = launch_qproj(fp32, S, c->jh.nS, st, ji, bdev)) != cudaSuccess) return e;
+      if (proj && (e = launch_qproj(fp32, S, nS, st, ji, bdev)) != cudaSuccess) return e;
       if ((e = launch_cocg_update(fp32, S, nB, st, ji, bdev)) != cudaSuccess) return e;
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 2], st, evf)) != cudaSuccess) return e;
       if ((e = launch_book(S, it, st, ji, bdev)) != cudaSuccess) return e;
@@ -1073,7 +1130,7 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
     return cudaSuccess;
   };
   const int per_iter = (proj ? 12 : 9) + (sh ? 3 : 0) + (goal ? 1 : 0);
-  const double vbytes = (double)N * (fp32 ? sizeof(float2) : sizeof(double2));
+  const double vbytes = (double)(pool ? pool->N : c->N) * (fp32 ? sizeof(float2) : sizeof(double2));
   cudaGraphExec_t gexec = nullptr;
   if (o->use_graph) {
     GraphKey key{fp32 ? 1 : 0, S, G, w.generation, proj ? 1 : 0, timing ? 1 : 0, ns, (sh ? sh->nT : 0) * 2 + (goal ? 1 : 0)};
@@ -1254,6 +1311,7 @@ static rsn_status apply_impl(rsn_ctx* c, int precision, int n_rhs, const double*
   b.junc = q.sys_junc.as<int>();
   b.E = q.sys_E.as<double>();
   b.voff = q.sys_xo.as<long long>();
+  b.pstride = c->n_proj;
   RSN_CUDA(c, cudaMemcpyAsync(c->bd.as<BatchDev>() + 1, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));
   const BatchDev* bdev = c->bd.as<BatchDev>() + 1;
   // bulk-copy kernels need 16-byte aligned vectors; otherwise a register tiling
@@ -1688,6 +1746,217 @@ rsn_status rsn_transmission_vjp_reuse(rsn_ctx* c, int n_e, const double* E, int 
                            reinterpret_cast<const double2*>(x_dev));
 }
 
+}  // extern "C"
+
+// Slot-pool description of several junctions for one precision: per-junction
+// tilings for `nslots` slots, one launch configuration per operator kind in
+// use (largest thread count, shared memory and tile count of its junctions).
+// Register-kernel junctions must agree on points per thread (a template
+// parameter); returns false if they do not.
+static bool make_pool(rsn_ctx* const* ctxs, int K, bool fp32, int nslots, PoolSpec& pool,
+                      std::vector<JuncDev>& js) {
+  pool = PoolSpec();
+  pool.K = K;
+  pool.R = ctxs[0]->R;
+  js.assign(2 * K, JuncDev{});
+  int ppt_reg = 0, ppt_res = 0;
+  for (int k = 0; k < K; ++k) {
+    rsn_ctx* c = ctxs[k];
+    const Tiling ti = choose_tiling(c, !fp32, OP_COCG, nslots), tr = choose_tiling(c, true, OP_RESID, nslots);
+    const int kind = ti.plane ? kOpPlane : ti.pair ? kOpPair : ti.tma ? kOpTma : kOpReg;
+    if (kind == kOpReg) {
+      if (ppt_reg && ppt_reg != ti.ppt) return false;
+      ppt_reg = ti.ppt;
+    }
+    if (ppt_res && ppt_res != tr.ppt) return false;
+    ppt_res = tr.ppt;
+    Tiling& L = pool.inner[kind];
+    if (!pool.has[kind]) L = ti;
+    pool.has[kind] = true;
+    L.threads = std::max(L.threads, ti.threads);
+    L.smem = std::max(L.smem, ti.smem);
+    L.n = std::max(L.n, ti.n);
+    L.big = L.big || ti.big;
+    if (k == 0) pool.resid = tr;
+    pool.resid.threads = std::max(pool.resid.threads, tr.threads);
+    pool.resid.smem = std::max(pool.resid.smem, tr.smem);
+    pool.resid.n = std::max(pool.resid.n, tr.n);
+    pool.N = std::max(pool.N, c->N);
+    pool.n_proj = std::max(pool.n_proj, c->n_proj);
+    pool.n_groups = std::max(pool.n_groups, c->n_groups);
+    pool.max_np = std::max(pool.max_np, c->max_np);
+    pool.nB = std::max(pool.nB, c->jh.nB);
+    pool.nS = std::max(pool.nS, c->jh.nS);
+    pool.PA = std::max(pool.PA, std::max(ti.n + c->n_groups, tr.n));
+    pool.PB = std::max(pool.PB, c->jh.nB);
+    for (int h = 0; h < 2; ++h) {
+      const Tiling& t = h == 0 ? ti : tr;
+      JuncDev& J = js[h * K + k];
+      J = c->jh;
+      J.TY = t.TY;
+      J.Lz = t.Lz;
+      J.ytiles = t.ytiles;
+      J.ztiles = t.ztiles;
+      J.nA = t.n;
+      J.nR = tr.n;
+      J.kind = h == 0 ? kind : kOpReg;
+    }
+  }
+  // the big point-pair variant serves every point-pair junction of the pool
+  if (pool.has[kOpPair] && pool.inner[kOpPair].threads > kPairThreads) pool.inner[kOpPair].big = true;
+  return true;
+}
+
+// rsn_batch_transmission on one slot pool: every (junction, energy, column)
+// system of the batch waits in one queue, and each slot works on its system's
+// junction, so uneven junctions share every launch.  The first context owns
+// the pool (stream, slots, graphs).
+static rsn_status batch_pool_impl(int K, rsn_ctx* const* ctxs, const int* n_e, const double* const* E,
+                                  const int* n_cols, const int32_t* const* cols, const rsn_solver_opts* o,
+                                  double* const* T, std::vector<rsn_status>& st) {
+  rsn_ctx* c = ctxs[0];
+  const bool fp32 = o->precision == RSN_MIXED;
+  RSN_CUDA(c, cudaSetDevice(c->device));
+  // order the pool's stream after every caller stream
+  for (int k = 0; k < K; ++k) {
+    RSN_CUDA(c, cudaEventRecord(ctxs[k]->ev_in, ctxs[k]->user_stream));
+    RSN_CUDA(c, cudaStreamWaitEvent(c->st, ctxs[k]->ev_in, 0));
+  }
+  reset_stats(c);
+  const auto t_start = std::chrono::steady_clock::now();
+  RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
+  StreamIn in;
+  std::vector<long long> sys0(K + 1, 0), e0(K + 1, 0);
+  std::vector<double> gr_all;
+  for (int k = 0; k < K; ++k) {
+    for (int e = 0; e < n_e[k]; ++e)
+      for (int j = 0; j < n_cols[k]; ++j) {
+        in.junc.push_back(k);
+        in.E.push_back(E[k][e]);
+        in.col.push_back(cols[k][j]);
+        in.dep.push_back(-1);
+        in.bn2.push_back(0.0);
+        in.xo.push_back(-1);
+        in.xfo.push_back(0);
+      }
+    sys0[k + 1] = (long long)in.E.size();
+    e0[k + 1] = e0[k] + n_e[k];
+    for (int j = 0; j < n_cols[k]; ++j) gr_all.push_back(ctxs[k]->gr[cols[k][j]]);
+  }
+  const long long nsys = sys0[K];
+  CallBufs& q = c->cb;
+  RSN_CUDA(c, q.gr_cols.ensure(std::max<size_t>(1, gr_all.size()) * sizeof(double)));
+  RSN_CUDA(c, q.Td.ensure(std::max<long long>(1, e0[K]) * sizeof(double)));
+  if (!gr_all.empty())
+    RSN_CUDA(c, cudaMemcpyAsync(q.gr_cols.p, gr_all.data(), gr_all.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                c->st));
+  std::vector<int> status(nsys, 0);
+  std::vector<int> iters(nsys, 0);
+  if (nsys > 0) {
+    auto run = [&](const rsn_solver_opts* oo, const StreamIn& sin, StreamOut& so) -> rsn_status {
+      const bool f32 = oo->precision == RSN_MIXED;
+      // slots first (a pool of one slot size), then the tilings for that count
+      PoolSpec probe;
+      std::vector<JuncDev> js;
+      probe.N = 0;
+      for (int k = 0; k < K; ++k) probe.N = std::max(probe.N, ctxs[k]->N);
+      const int S = choose_slots(c, oo, (long long)sin.E.size(), 0, 0, probe.N);
+      rsn_solver_opts o2 = *oo;
+      o2.rhs_block = S;
+      PoolSpec pool;
+      if (!make_pool(ctxs, K, f32, S, pool, js)) RSN_FAIL(c, RSN_EINVAL, "pool: junctions need different kernels");
+      RSN_CUDA(c, c->pool_jd.ensure(js.size() * sizeof(JuncDev)));
+      RSN_CUDA(c, cudaMemcpyAsync(c->pool_jd.p, js.data(), js.size() * sizeof(JuncDev), cudaMemcpyHostToDevice, c->st));
+      RSN_CUDA(c, cudaStreamSynchronize(c->st));  // js lives on the host stack
+      pool.ji = c->pool_jd.as<JuncDev>();
+      pool.jr = c->pool_jd.as<JuncDev>() + K;
+      // graphs captured for another configuration must not be replayed
+      clear_graphs(c);
+      c->ws.generation++;
+      return run_stream(c, &o2, sin, nullptr, nullptr, true, 0, t_start, so, nullptr, &pool);
+    };
+    StreamOut so;
+    rsn_status rs = run(o, in, so);
+    if (rs != RSN_OK) return rs;
+    RSN_CUDA(c, q.t_all.ensure(nsys * sizeof(double)));
+    RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, q.out_t.p, nsys * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    if (fp32) {
+      // systems whose FP32 recurrence stalled are solved again in FP64 (same pool)
+      std::vector<long long> F;
+      StreamIn sub;
+      for (long long k = 0; k < nsys; ++k)
+        if (so.status[k] != 0) {
+          F.push_back(k);
+          sub.push(in, (size_t)k);
+          sub.bn2.back() = 0.0;
+        }
+      if (!F.empty()) {
+        rsn_solver_opts o64;
+        rsn_default_opts(RSN_FP64, &o64);
+        o64.tol = o->tol;
+        o64.tol_T = o->tol_T;
+        o64.deadline_ms = o->deadline_ms;
+        o64.use_graph = o->use_graph;
+        o64.graph_iters = o->graph_iters;
+        StreamOut s2;
+        if ((rs = run(&o64, sub, s2)) != RSN_OK) return rs;
+        for (size_t f = 0; f < F.size(); ++f) {
+          so.status[F[f]] = s2.status[f];
+          so.iters[F[f]] += s2.iters[f];
+          so.relres[F[f]] = s2.relres[f];
+          RSN_CUDA(c, cudaMemcpyAsync(q.t_all.as<double>() + F[f], q.out_t.as<double>() + f, sizeof(double),
+                                      cudaMemcpyDeviceToDevice, c->st));
+        }
+        c->st_fallback += (int64_t)F.size();
+      }
+    }
+    for (int k = 0; k < K; ++k) {
+      if (n_e[k] == 0) continue;
+      if (n_cols[k] == 0) {
+        RSN_CUDA(c, cudaMemsetAsync(q.Td.as<double>() + e0[k], 0, n_e[k] * sizeof(double), c->st));
+        continue;
+      }
+      long long c0 = 0;
+      for (int l = 0; l < k; ++l) c0 += n_cols[l];
+      RSN_CUDA(c, launch_t_final(n_e[k], n_cols[k], c->st, q.t_all.as<double>() + sys0[k],
+                                 q.gr_cols.as<double>() + c0, q.Td.as<double>() + e0[k]));
+    }
+    for (long long k = 0; k < nsys; ++k) status[k] = so.status[k], iters[k] = so.iters[k];
+    for (int k = 0; k < K; ++k) {
+      std::string why;
+      StreamOut part;
+      part.status.assign(so.status.begin() + sys0[k], so.status.begin() + sys0[k + 1]);
+      part.iters.assign(so.iters.begin() + sys0[k], so.iters.begin() + sys0[k + 1]);
+      part.relres.assign(so.relres.begin() + sys0[k], so.relres.begin() + sys0[k + 1]);
+      part.timeout = so.timeout;
+      const rsn_status ks = stream_status(part, 0, sys0[k + 1] - sys0[k], nullptr, nullptr, &why);
+      if (ks != RSN_OK) {
+        st[k] = ks;
+        char buf[600];
+        snprintf(buf, sizeof(buf), "some systems did not reach tol: %s", why.c_str());
+        ctxs[k]->err = buf;
+      }
+    }
+  }
+  RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
+  for (int k = 0; k < K; ++k)
+    if (n_e[k] > 0)
+      RSN_CUDA(c, cudaMemcpyAsync(T[k], q.Td.as<double>() + e0[k], n_e[k] * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->st));
+  RSN_CUDA(c, cudaStreamSynchronize(c->st));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->t0, c->t1);
+  c->st_ms = ms;
+  clear_graphs(c);
+  c->ws.generation++;
+  // every caller stream waits for the pool's work
+  RSN_CUDA(c, cudaEventRecord(c->ev_out, c->st));
+  for (int k = 0; k < K; ++k) RSN_CUDA(c, cudaStreamWaitEvent(ctxs[k]->user_stream, c->ev_out, 0));
+  return RSN_OK;
+}
+
+extern "C" {
+
 rsn_status rsn_batch_transmission(int n_ctx, rsn_ctx* const* ctxs, const int* n_e, const double* const* E,
                                   const int* n_cols, const int32_t* const* cols, const rsn_solver_opts* opts,
                                   double* const* T, rsn_status* status) {
@@ -1702,6 +1971,50 @@ rsn_status rsn_batch_transmission(int n_ctx, rsn_ctx* const* ctxs, const int* n_
   rsn_solver_opts base;
   if (opts) base = *opts;
   else rsn_default_opts(RSN_MIXED, &base);
+  // one slot pool when every junction is on the same device with the same FD
+  // order and no explicit slot count was asked for
+  bool pooled = n_ctx > 1 && base.rhs_block <= 0;
+  for (int k = 0; k < n_ctx && pooled; ++k) pooled = ctxs[k]->device == ctxs[0]->device && ctxs[k]->R == ctxs[0]->R;
+  if (pooled) {
+    std::vector<rsn_status> st(n_ctx, RSN_OK);
+    for (int k = 0; k < n_ctx; ++k) {
+      rsn_ctx* c = ctxs[k];
+      rsn_status rs = RSN_OK;
+      if (n_e[k] > 0 && !T[k]) {
+        c->err = "T is NULL";
+        rs = RSN_EINVAL;
+      }
+      if (rs == RSN_OK) rs = commit_setup(c);
+      if (rs == RSN_OK) rs = check_solve_args(c, n_e[k], E[k], n_cols[k], cols[k], &base);
+      st[k] = rs;
+    }
+    int bad = -1;
+    for (int k = 0; k < n_ctx && bad < 0; ++k)
+      if (st[k] != RSN_OK) bad = k;
+    if (bad >= 0) {
+      // the pool runs all junctions or none
+      for (int k = 0; k < n_ctx; ++k)
+        if (st[k] == RSN_OK) {
+          st[k] = RSN_EINVAL;
+          ctxs[k]->err = "rsn_batch_transmission: not run, the arguments of junction " + std::to_string(bad) +
+                         " were refused";
+        }
+    } else {
+      const rsn_status rs = batch_pool_impl(n_ctx, ctxs, n_e, E, n_cols, cols, &base, T, st);
+      if (rs != RSN_OK)
+        for (int k = 0; k < n_ctx; ++k)
+          if (st[k] == RSN_OK) {
+            st[k] = rs;
+            if (k) ctxs[k]->err = "rsn_batch_transmission: the slot pool failed: " + ctxs[0]->err;
+          }
+    }
+    rsn_status worst = RSN_OK;
+    for (int k = 0; k < n_ctx; ++k) {
+      if (status) status[k] = st[k];
+      if (worst == RSN_OK && st[k] != RSN_OK) worst = st[k];
+    }
+    return worst;
+  }
   // per-context options: without an explicit slot count, each context's pool
   // is capped by its share of the free memory of its device
   std::vector<rsn_solver_opts> ok(n_ctx, base);
@@ -1972,6 +2285,7 @@ static rsn_status apply_noalloc_impl(rsn_ctx* c, int precision, int n_rhs, const
   b.E = reinterpret_cast<double*>(base + o_E);
   b.voff = reinterpret_cast<long long*>(base + o_voff);
   b.junc = reinterpret_cast<int*>(base + o_junc);
+  b.pstride = c->n_proj;
   void* cbuf = base + o_c;
   const BatchDev* bdev = reinterpret_cast<const BatchDev*>(base);
   RSN_CUDA(c, cudaMemcpyAsync(base, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));

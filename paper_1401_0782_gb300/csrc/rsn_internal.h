@@ -42,6 +42,7 @@ struct JuncDev {
   long long N;
   // stencil tiling of the operator kernel for this junction
   int TY, Lz, ytiles, ztiles, nA;  // nA = ytiles*ztiles CTAs per slot (this launch's tiling)
+  int kind;                        // operator kernel of this junction's slots: kOpReg, kOpTma, kOpPair, kOpPlane
   int nR;                          // CTAs per slot of the true-residual kernel (rho_0, ||r_0||^2 partials)
   int nB;                          // streaming-kernel CTAs per slot
   double w64[kMaxR + 1];           // w[m] = c_m / (2 h^2), m = 1..R (w[0] unused)
@@ -133,6 +134,7 @@ struct BatchDev {
   double2* rho_part;    // [S][PB] COCG update kernel: r^T r
   double* nrm_part;     // [S][PB]
   double2* mu_part;     // [S][PA] operator kernel: p^T A p
+  int pstride;          // per-slot stride of the projection arrays (the largest n_proj of the junctions)
   void* c_r;            // [S][n_proj] projections of r (inner precision)
   void* c_p;            // [2][S][n_proj] projections of p
   double2* c_x;         // [S][n_proj] projections of x64 + d (FP64)
@@ -190,6 +192,9 @@ struct BatchDev {
 };
 
 enum OpMode { OP_COCG = 0, OP_RESID = 1, OP_APPLY = 2 };
+// operator kernels; a slot pool over several junctions launches each kind its
+// junctions use, and every kernel skips the slots of junctions of another kind
+enum OpKind { kOpReg = 0, kOpTma = 1, kOpPair = 2, kOpPlane = 3 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
 cudaError_t launch_op(int mode, bool fp32, int R, int ppt, dim3 grid, int threads, size_t smem,
@@ -220,7 +225,8 @@ cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const Ju
 cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
                                const BatchDev* b);
 cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, int max_np, cudaStream_t st,
-                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out);
+                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out,
+                           bool one_slot_per_cta = false);
 cudaError_t launch_book(int nslots, int slot_it, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 constexpr int kBookWarps = 8;  // slots per CTA of the bookkeeping kernel (one warp each)
 cudaError_t launch_sched(int nslots, int slot_it, cudaStream_t st, const JuncDev* jt, const BatchDev* b);

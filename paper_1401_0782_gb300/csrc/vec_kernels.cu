@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
     for (int u = 0; u < SPB; ++u) {
       if (slot[u] < 0) continue;  // uniform across the CTA
       const int sl = slot[u];
-      C* out = reinterpret_cast<C*>(c_out) + (size_t)sl * J.n_proj + p0;
+      C* out = reinterpret_cast<C*>(c_out) + (size_t)sl * b.pstride + p0;
       // PJ_R, thread 0: the projections of the new direction
       // c_p = c_r + beta c_p_old (c_p = c_r in the first iteration), e_kb c_p
       // for the update kernel, and this atom's share of mu = p^T A p,
@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
             out[p] = cr;
             if constexpr (MODE == PJ_R) {
               const int k = b.iters[sl];
-              const C* cpo = reinterpret_cast<const C*>(b.c_p) + ((size_t)(k & 1) * b.nslots + sl) * J.n_proj;
-              C* cpn = reinterpret_cast<C*>(b.c_p) + ((size_t)((k + 1) & 1) * b.nslots + sl) * J.n_proj;
+              const C* cpo = reinterpret_cast<const C*>(b.c_p) + ((size_t)(k & 1) * b.nslots + sl) * b.pstride;
+              C* cpn = reinterpret_cast<C*>(b.c_p) + ((size_t)((k + 1) & 1) * b.nslots + sl) * b.pstride;
               C* cen = reinterpret_cast<C*>(b.c_e) + (size_t)sl * b.ce_stride;
               C c = cr;
               if (k > 0) c = cfma(from64<C>(b.beta_cur[sl]), cpo[p0 + p], c);
@@ -1059,9 +1059,16 @@ static void launch_project_np(int mode, bool fp32, dim3 grid, cudaStream_t st, c
 }
 
 cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, int max_np, cudaStream_t st,
-                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out) {
-  // slots per CTA: the projector values of an atom are loaded once for all of them
-  if (max_np <= 4) {
+                           const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out,
+                           bool one_slot_per_cta) {
+  // slots per CTA: the projector values of an atom are loaded once for all of
+  // them; a pool over several junctions takes one slot per CTA (atom g differs
+  // between junctions)
+  if (one_slot_per_cta && max_np <= 4) {
+    launch_project_np<4, 1>(mode, fp32, dim3(n_groups, nslots), st, jt, b, x_in, c_out);
+  } else if (one_slot_per_cta && max_np <= 9) {
+    launch_project_np<9, 1>(mode, fp32, dim3(n_groups, nslots), st, jt, b, x_in, c_out);
+  } else if (max_np <= 4) {
     launch_project_np<4, 4>(mode, fp32, dim3(n_groups, (nslots + 3) / 4), st, jt, b, x_in, c_out);
   } else if (max_np <= 9) {
     launch_project_np<9, 2>(mode, fp32, dim3(n_groups, (nslots + 1) / 2), st, jt, b, x_in, c_out);

@@ -8,7 +8,7 @@ at this size needs tens of GB): forward columns x_c = G e_c (Eq. G), then
 lambda_c = G (Gamma_L o conj x_c) with the same operator (G = G^T, Eq.
 complex-sym), T = 4 sum_c Gamma_R,c sum_L Gamma_L |x_c|^2 (Eq. T-realspace)
 and dT/dV_r = 8 sum_c Gamma_R,c Re(lambda_c(r) x_c(r)).  Every solve is
-certified by its true residual (relative 1e-11 forward, 1e-10 adjoint).  The
+certified by its true residual (relative 1e-13 forward, 1e-10 adjoint).  The
 file keeps T, sum_r dT/dV_r, and dT/dV at 64 seeded points where the gradient
 is large (the FD points of the tests among them).  Only ``oracle`` and the
 input generators are used.
@@ -33,7 +33,7 @@ def main() -> None:
     j = P.adjoint_junction(seed=4)
     cols = P.column_subset(j, 4, seed=11)
     E = 0.2
-    X, solver = O.solve_columns(j, E, cols, return_lu=True, method="krylov", rtol=1e-11)
+    X, solver = O.solve_columns(j, E, cols, return_lu=True, method="krylov", rtol=1e-13)
     T = 4.0 * np.sum(j.gamma_r[cols] * O.column_weights(j, X))
     solver.rtol = 1e-10
     W = j.gamma_l[:, None] * np.conj(X)
@@ -44,7 +44,7 @@ def main() -> None:
     with open(OUT, "w") as f:
         f.write("# dT(E)/dV_loc(r) on problems.adjoint_junction(seed=4) (48x48x192), E = 0.2 Ha,\n")
         f.write(f"# columns problems.column_subset(j, 4, seed=11) = {' '.join(str(int(c)) for c in cols)}\n")
-        f.write("# oracle Krylov route (forward relative residual 1e-11, adjoint 1e-10, both certified)\n")
+        f.write("# oracle Krylov route (forward relative residual 1e-13, adjoint 1e-10, both certified)\n")
         f.write("# written by tests/golden/make_adjoint_golden.py (oracle only)\n")
         f.write(f"T {T:.17e}\n")
         f.write(f"sum_g {g.sum():.17e}\n")

@@ -1,6 +1,7 @@
-"""Batched uneven junctions through rsn_batch_transmission: each junction's
-T(E) against the same junction solved alone and against the CPU oracle (sparse
-LU), in FP64 and mixed precision; error reporting per junction."""
+"""Batched uneven junctions through rsn_batch_transmission (one slot pool over
+all the junctions of a device): each junction's T(E) against the same junction
+solved alone and against the CPU oracle (sparse LU), in FP64 and mixed
+precision; error reporting per junction."""
 import numpy as np
 import pytest
 
@@ -61,5 +62,31 @@ def test_batch_reports_the_failing_junction(B):
     with pytest.raises(B.RsnError) as e:
         B.batch_transmission([ctxs[0], ctxs[0]], [[0.2], [0.2]], None, B.default_opts(B.RSN_FP64))
     assert e.value.code == B.RSN_EINVAL
+    for c in ctxs:
+        c.close()
+
+
+def test_one_pool_over_sixteen_uneven_junctions(B):
+    # the 16 smallest of the 64 seeded uneven junctions (cross-sections 12..21,
+    # odd and even, so the pool runs the point-pair and the register kernel
+    # side by side): pooled T against each junction alone, and against the
+    # oracle's LU on the three smallest
+    js = P.batched_junctions()
+    pick = sorted(range(len(js)), key=lambda k: js[k].N)[:16]
+    sub = [js[k] for k in pick]
+    assert len({j.nx % 2 for j in sub}) == 2
+    ctxs = [B.Context(0).set_junction(j) for j in sub]
+    energies = [np.array([0.18, 0.22]) for _ in sub]
+    cols = [j.right_columns()[::97] for j in sub]
+    for prec in (B.RSN_FP64, B.RSN_MIXED):
+        o = B.default_opts(prec)
+        Tb = B.batch_transmission(ctxs, energies, cols, o)
+        rel = 1e-8 if prec == B.RSN_FP64 else 1e-6
+        for k, (j, ctx) in enumerate(zip(sub, ctxs)):
+            T_alone = ctx.transmission(energies[k], cols[k], o)
+            assert np.all(np.abs(Tb[k] - T_alone) <= rel * np.abs(T_alone)), (k, Tb[k], T_alone)
+            if prec == B.RSN_FP64 and k < 3:
+                T_ref = O.transmission(j, energies[k], cols[k])
+                assert np.all(np.abs(Tb[k] - T_ref) <= 1e-8 * np.abs(T_ref)), (k, Tb[k], T_ref)
     for c in ctxs:
         c.close()
