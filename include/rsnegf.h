@@ -93,13 +93,16 @@ typedef struct {
                            Eq. T-realspace -- changes by at most tol_T * t_j between two true
                            residuals.  Where every lead channel is closed, x_j is exponentially
                            small on the Gamma_L support and a residual of tol relative to the
-                           whole column fixes t_j only to ~1e-4 (tol 1e-10) or ~1e-7 (1e-13);
+                           whole column fixes t_j only to ~1e-3 (tol 1e-10) or ~1e-6 (1e-13);
                            the iterate keeps converging there after its residual reaches the
-                           rounding floor.  0 = residual criterion alone. */
+                           rounding floor.  Measured on the 24x24x120 junction: tol_T 1e-6
+                           (mixed default) leaves each t_j within ~1e-5 and T within ~1e-7 of
+                           the FP64 columns; 1e-10 (FP64 default) within ~1e-11.
+                           0 = residual criterion alone. */
 } rsn_solver_opts;
 
 /* Defaults for a precision: FP64 -> tol 1e-13, tol_T 1e-10, tol_inner 1e-6,
-   max_iter 20000; MIXED -> tol 1e-10, tol_T 1e-7, tol_inner 1e-1, max_iter 3000
+   max_iter 20000; MIXED -> tol 1e-10, tol_T 1e-6, tol_inner 1e-1, max_iter 3000
    (a system that needs more, or whose FP32 recurrence stalls, is solved again
    in FP64 from zero);
    both: tol_adjoint 0 (= tol), max_outer 64, graphs on (16 iterations per
@@ -272,6 +275,19 @@ rsn_status rsn_transmission_vjp(rsn_ctx* ctx, int n_e, const double* E, int n_co
                                 const double* T_bar, double* dV, int dV_is_device,
                                 double* T);
 
+/* Landauer current (Sec. II.A, Eq. Landauer):
+     I(V_k) = (2e/h) int T(E) [f(E - mu_L) - f(E - mu_R)] dE,  mu_{L,R} = E_F +- V_k / 2,
+   f the Fermi-Dirac occupation at temperature kT (hartree; kT = 0: a step with
+   f(0) = 1/2).  Atomic units: e = hbar = 1, so 2e/h = 1/pi, energies and the
+   bias eV in hartree, I in e E_h / hbar (6.62 mA); the factor 2 is the spin.
+   The integral is the trapezoidal rule on the grid E (host, n_e strictly
+   ascending doubles) with T (host, n_e doubles, e.g. from
+   rsn_transmission_shifted); T is taken as zero outside the grid.  One kernel
+   on the context's stream, FP64, fixed-order sums.  I: host, n_v doubles.
+   Errors: RSN_EINVAL (NULL, unsorted or non-finite input, kT < 0). */
+rsn_status rsn_landauer_current(rsn_ctx* ctx, int n_e, const double* E, const double* T, int n_v,
+                                const double* V, double E_F, double kT, double* I);
+
 /* Counters of the last solve on this context: total Krylov iterations over all
    systems, true-residual replacements (reliable updates), device kernel
    launches queued, elapsed GPU milliseconds of the solve phase, and the number
@@ -284,7 +300,8 @@ rsn_status rsn_last_stats(const rsn_ctx* ctx, int64_t* krylov_iters, int64_t* sw
 
 /* Live per-kernel timing of the last solve call made with opts.timing = 1.
    kind 0: the fused COCG operator kernel (p = r + beta p, q = A p, p^T q);
-   kind 1: the COCG update kernel (r -= alpha q, d += alpha p, r^T r).
+   kind 1: the COCG update kernel (projector term of q on the support points,
+   r -= alpha q, d += alpha p, r^T r).
    launches: launches timed; ms: summed CUDA-event durations on the library's
    stream; bytes: algorithmic HBM bytes of those launches (vectors read and
    written once per active system: 4 vectors for kind 0, 6 for kind 1).
@@ -307,7 +324,9 @@ rsn_status rsn_bench_kernel(rsn_ctx* ctx, int precision, int kind, int nslots, i
    set of tilings of this grid -- the FP32 plane kernel, the point-pair kernel
    and the whole-plane bulk-copy kernel with several z-chunk lengths, and the
    register-prefetch kernel over rows per tile, points per thread and z-chunks
-   -- and keeps the fastest on the context.  Outputs (any may be NULL): the
+   -- and keeps on the context the one with the least launch time with all
+   nslots systems active plus with a quarter of them active (the tail of a
+   solve, where long z chunks leave SMs idle).  Outputs (any may be NULL): the
    chosen TY, Lz, ppt (0 = automatic), tma (3: the plane kernel, 2: the
    point-pair kernel, 1: the whole-plane bulk-copy kernel, 0: the register
    kernel) and its algorithmic GB/s.  Errors: as rsn_bench_kernel; RSN_ECUDA

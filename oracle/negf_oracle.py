@@ -32,6 +32,8 @@ checked by eye against the paper:
 * ``transmission_trace``   -- Eq. T written as a dense trace, Tr{G Gam_R G^dag Gam_L}.
 * ``transmission_eigen``   -- Eq. T-tilde-realsp from a full complex-orthogonal
                               eigenbasis (Sec. II.C), tiny grids only.
+* ``landauer_current``     -- Eq. Landauer, I = (2e/h) int T (f_L - f_R) dE, by the
+                              trapezoidal rule on the given energy grid.
 * ``open_channels``        -- closed-form channel count of a hard-wall waveguide.
 * ``lead_self_energy_T``   -- exact semi-infinite-lead self-energies for the
                               same waveguide (textbook NEGF), dense.
@@ -66,6 +68,7 @@ __all__ = [
     "transmission_eigen",
     "open_channels",
     "channel_thresholds",
+    "landauer_current",
     "lead_self_energy_T",
     "apply_operator",
     "local_hamiltonian",
@@ -430,6 +433,31 @@ def transmission_eigen(j, energies: Iterable[float]) -> np.ndarray:
         dj = 1.0 / (E - eps)  # 1/(E - eps_j)
         di = 1.0 / (E - np.conj(eps))  # 1/(E - eps_i^*)
         out.append(np.real(np.sum(GtL * GtR.T * di[:, None] * dj[None, :])))
+    return np.asarray(out)
+
+
+def fermi(x: np.ndarray, kT: float) -> np.ndarray:
+    """Fermi-Dirac occupation f(x) = 1 / (1 + exp(x / kT)) of an energy x
+    measured from the chemical potential; kT = 0: step with f(0) = 1/2."""
+    x = np.asarray(x, dtype=float)
+    if kT == 0.0:
+        return np.where(x < 0, 1.0, np.where(x > 0, 0.0, 0.5))
+    return 0.5 * (1.0 - np.tanh(x / (2.0 * kT)))
+
+
+def landauer_current(E: Sequence[float], T: Sequence[float], V: Sequence[float], E_F: float = 0.0,
+                     kT: float = 0.0) -> np.ndarray:
+    """Eq. Landauer: I(V) = (2e/h) int T(E) [f(E - mu_L) - f(E - mu_R)] dE,
+    mu_{L,R} = E_F +- V/2 (Sec. II.A: the electrodes' chemical potentials sit at
+    +-eV/2 about the Fermi level).  Atomic units (e = hbar = 1, so 2e/h = 1/pi;
+    energies and the bias eV in hartree, I in e E_h / hbar).  The integral is
+    the trapezoidal rule on the ascending grid E where T is given."""
+    E = np.asarray(E, dtype=float)
+    T = np.asarray(T, dtype=float)
+    out = []
+    for v in np.atleast_1d(V):
+        g = T * (fermi(E - (E_F + 0.5 * v), kT) - fermi(E - (E_F - 0.5 * v), kT))
+        out.append(np.sum(0.5 * (E[1:] - E[:-1]) * (g[1:] + g[:-1])) / np.pi)
     return np.asarray(out)
 
 

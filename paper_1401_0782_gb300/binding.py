@@ -47,6 +47,8 @@ _SIGS = {
                                          ct.c_void_p, ct.c_void_p]),
     "rsn_transmission_vjp_reuse": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
                                               ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
+    "rsn_landauer_current": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p,
+                                        ct.c_double, ct.c_double, ct.c_void_p]),
     "rsn_batch_transmission": (ct.c_int, [ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                           ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_last_stats": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
@@ -315,6 +317,20 @@ class Context:
                     self.lib.rsn_transmission_vjp_reuse(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
                                                         ct.byref(opts), x.data_ptr(), _ptr(Tb), dptr, isdev))
         return dV
+
+    def landauer_current(self, E: Sequence[float], T: Sequence[float], V: Sequence[float], E_F: float = 0.0,
+                         kT: float = 0.0) -> np.ndarray:
+        """I(V) of Eq. Landauer in atomic units (e E_h / hbar) from T on the grid E."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        V = np.ascontiguousarray(np.atleast_1d(V), dtype=np.float64)
+        if T.size != E.size:
+            raise ValueError("T must have one value per energy")
+        I = np.zeros(V.size, np.float64)
+        self._check("rsn_landauer_current",
+                    self.lib.rsn_landauer_current(self.h, int(E.size), _ptr(E), _ptr(T), int(V.size), _ptr(V),
+                                                  float(E_F), float(kT), _ptr(I)))
+        return I
 
     def kernel_stats(self, kind: int):
         """(launches, ms, algorithmic bytes) of kind 0 (COCG operator) / 1 (COCG update)."""

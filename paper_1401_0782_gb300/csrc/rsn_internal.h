@@ -24,7 +24,8 @@ constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
 constexpr int kCePad = 16;
 constexpr int kMaxGraphIters = 256;
 constexpr int kMaxApplyRhs = 65535;
-constexpr int kMaxGoalChecks = 24;   // true residuals of a goal phase before its iterate is kept  // vectors per operator-application call (grid y dimension)
+constexpr int kMaxGoalChecks = 24;   // T checks of a goal phase before its iterate is kept
+constexpr int kGoalCycle = 40;       // iterations between T checks at most (or a tenfold cut of the recurrence)  // vectors per operator-application call (grid y dimension)
 constexpr int kSchedThreads = 1024;
 // CTA rows of the kernels that work only on NEW / CHECK slots (zero, true
 // residual and its projections, x update): each row takes list entries
@@ -222,7 +223,9 @@ cudaError_t launch_op_plane(int mode, int R, dim3 grid, int threads, size_t smem
                             const BatchDev* b, const void* x_in, void* y_out, const void* c_in);
 
 cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
-cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
+// the COCG update with the projector term of q on the support points; ce_stride:
+// per-slot entries of e_kb c_p (BatchDev::ce_stride), staged in shared memory
+cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, int ce_stride, cudaStream_t st, const JuncDev* jt,
                                const BatchDev* b);
 cudaError_t launch_project(int mode, bool fp32, int nslots, int n_groups, int max_np, cudaStream_t st,
                            const JuncDev* jt, const BatchDev* b, const void* x_in, void* c_out,
@@ -234,8 +237,9 @@ cudaError_t launch_x_update(bool fp32, int nslots, int nB, cudaStream_t st, cons
                             const BatchDev* b);
 cudaError_t launch_emit(int nslots, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_list(cudaStream_t st, const BatchDev* b);
+cudaError_t launch_landauer(int n_e, const double* E, const double* T, int n_v, const double* V, double E_F,
+                            double kT, double* I, cudaStream_t st);
 cudaError_t launch_tgoal(cudaStream_t st, const JuncDev* jt, const BatchDev* b);
-cudaError_t launch_qproj(bool fp32, int nslots, int nS, cudaStream_t st, const JuncDev* jt, const BatchDev* b);
 cudaError_t launch_t_final(int n_e, int n_cols, cudaStream_t st, const double* t_all,
                            const double* gr_cols, double* T_out);
 // shifted systems: initialisation of NEW slots, the per-iteration update of

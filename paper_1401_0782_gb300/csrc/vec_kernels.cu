@@ -80,6 +80,10 @@ __global__ void __launch_bounds__(kVecThreads) zero_kernel(const JuncDev* __rest
 // COCG update (after the operator kernel of the same iteration):
 //   alpha = rho_k / mu_k,  r -= alpha q,  d += alpha p_new,
 //   partial sums of rho_{k+1} = r^T r and ||r||^2.
+// q arrives without the projector term (the operator kernel leaves it out);
+// on the points inside a projector support the term -sum_p v_p(i) e_kb[p] c_p
+// is added here, from e_kb c_p of the new direction (projection kernel, staged
+// in shared memory with its zero-padded tail), so q is never written back.
 // Each CTA covers kVecPts consecutive points of one system.  A non-finite
 // alpha leaves r and d untouched and flags the slot through a NaN norm.
 // ---------------------------------------------------------------------------
@@ -95,7 +99,14 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
   __shared__ double red[32 * 3];
   __shared__ double2 s_mu[kVecThreads];
   __shared__ double2 s_alpha;
+  extern __shared__ __align__(16) unsigned char upd_smem[];
+  C* s_ce = reinterpret_cast<C*>(upd_smem);  // e_kb c_p of the new direction, ce_stride entries
   const int k = b.iters[s];
+  const int np = J.n_proj;
+  if (np > 0) {
+    const C* cen = reinterpret_cast<const C*>(b.c_e) + (size_t)s * b.ce_stride;
+    for (int p = threadIdx.x; p < b.ce_stride; p += kVecThreads) s_ce[p] = cen[p];
+  }
   // mu = p^T A p from the operator kernel's partials (any number of tiles)
   // followed by one partial per atom from the projection kernel: thread t adds
   // partials t, t + 256, ... and thread 0 adds those sums in thread order, so
@@ -136,10 +147,18 @@ __global__ void __launch_bounds__(kVecThreads) cocg_update_kernel(const JuncDev*
   const long long i0 = (long long)blockIdx.x * kVecPts;
   const long long i1 = min(i0 + (long long)kVecPts, J.N);
   T nrm = 0, rre = 0, rim = 0;
+  const int nq = J.inv_nq;
   for (long long i = i0 + threadIdx.x; i < i1; i += kVecThreads) {
     const long long g = vo + i;
     const C p = pn[g];
-    const C q = qv[g];
+    C q = qv[g];
+    if (np > 0) {
+      const int e0 = J.inv_ptr[i], e1 = J.inv_ptr[i + 1];
+      for (int e = e0; e < e1; ++e) {
+        const C* cp = s_ce + J.inv_p0[e];
+        for (int qd = 0; qd < nq; ++qd) q = proj_quad<C, T>(J, e * nq + qd, cp + 4 * qd, q);
+      }
+    }
     C r = rv[g];
     r.x -= alpha.x * q.x - alpha.y * q.y;
     r.y -= alpha.x * q.y + alpha.y * q.x;
@@ -309,45 +328,6 @@ __global__ void __launch_bounds__(128) project_kernel(const JuncDev* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// Projector term of q = A p (the operator kernel leaves it out): for the grid
-// points inside a projector support, q(i) -= sum over the atom entries of i of
-// v_p(i) e_kb[p] c_p, with e_kb c_p of the new direction from the projection
-// kernel (zero-padded after the last projector).  ACTIVE slots.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads) qproj_kernel(const JuncDev* __restrict__ jt,
-                                                            const BatchDev* __restrict__ bp) {
-  using C = typename cx<T>::t;
-  const BatchDev& b = *bp;
-  const int s = blockIdx.y;
-  if (b.state[s] != SL_ACTIVE) return;
-  const JuncDev& J = jt[b.junc[s]];
-  if ((int)blockIdx.x >= J.nS) return;
-  const int nq = J.inv_nq;
-  const C* cen = reinterpret_cast<const C*>(b.c_e) + (size_t)s * b.ce_stride;
-  C* qv = reinterpret_cast<C*>(b.q) + b.voff[s];
-  const int k0 = blockIdx.x * kVecPts, k1 = min(k0 + kVecPts, J.n_sup);
-  for (int k = k0 + threadIdx.x; k < k1; k += kVecThreads) {
-    const int i = J.sup_pts[k];
-    const int e0 = J.inv_ptr[i], e1 = J.inv_ptr[i + 1];
-    C q = qv[i];
-    for (int e = e0; e < e1; ++e) {
-      const C* cp = cen + J.inv_p0[e];
-      for (int qd = 0; qd < nq; ++qd) q = proj_quad<C, T>(J, e * nq + qd, cp + 4 * qd, q);
-    }
-    qv[i] = q;
-  }
-}
-
-cudaError_t launch_qproj(bool fp32, int nslots, int nS, cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
-  if (nS <= 0) return cudaSuccess;
-  dim3 grid(nS, nslots);
-  if (fp32) qproj_kernel<float><<<grid, kVecThreads, 0, st>>>(jt, b);
-  else qproj_kernel<double><<<grid, kVecThreads, 0, st>>>(jt, b);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Bookkeeping after each COCG iteration, one warp per slot: rho_{k+1} and
 // ||r||^2 from the update kernel's partials (fixed-order warp tree),
 // beta_{k+1} = rho_{k+1} / rho_k, iteration counts, the recurrence target of
@@ -390,7 +370,7 @@ __global__ void __launch_bounds__(32 * kBookWarps) book_kernel(const JuncDev* __
     b.restart[s] = 1;
     b.rrec2[s] = 0.0;
     b.state[s] = SL_CHECK;
-  } else if (nrm <= b.tol2[s] || tot >= b.max_iter || cyc >= b.cycle_cap) {
+  } else if (nrm <= b.tol2[s] || tot >= b.max_iter || cyc >= b.cycle_cap || (b.gphase[s] && cyc >= kGoalCycle)) {
     b.rrec2[s] = nrm;
     b.state[s] = b.gphase[s] ? SL_CHECKT : SL_CHECK;
   }
@@ -937,6 +917,35 @@ __global__ void __launch_bounds__(256) shift_emit_kernel(const JuncDev* __restri
 }
 
 // ---------------------------------------------------------------------------
+// Landauer current (Eq. Landauer): I(V_k) = (2e/h) int T(E) [f(E - mu_L) -
+// f(E - mu_R)] dE with mu_{L,R} = E_F +- V_k / 2, atomic units (2e/h = 1/pi),
+// by the trapezoidal rule on the given ascending energy grid; one CTA per
+// bias, fixed-order sums.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fermi_dev(double x, double kT) {
+  if (kT == 0.0) return x < 0.0 ? 1.0 : (x > 0.0 ? 0.0 : 0.5);
+  return 0.5 * (1.0 - tanh(x / (2.0 * kT)));
+}
+
+__global__ void __launch_bounds__(256) landauer_kernel(int n_e, const double* __restrict__ E,
+                                                       const double* __restrict__ T, const double* __restrict__ V,
+                                                       double E_F, double kT, double* __restrict__ I) {
+  __shared__ double red[32];
+  const double v = V[blockIdx.x];
+  const double muL = E_F + 0.5 * v, muR = E_F - 0.5 * v;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e + 1 < n_e; e += blockDim.x) {
+    const double g0 = T[e] * (fermi_dev(E[e] - muL, kT) - fermi_dev(E[e] - muR, kT));
+    const double g1 = T[e + 1] * (fermi_dev(E[e + 1] - muL, kT) - fermi_dev(E[e + 1] - muR, kT));
+    acc += 0.5 * (E[e + 1] - E[e]) * (g0 + g1);
+  }
+  double vv[1] = {acc};
+  double out[1];
+  block_sum<1>(vv, red, out);
+  if (threadIdx.x == 0) I[blockIdx.x] = out[0] / 3.14159265358979323846;
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 #define RSN_DECL_OP(R)                                                                                        \
@@ -1035,11 +1044,18 @@ cudaError_t launch_zero(bool fp32, int nslots, int nB, cudaStream_t st, const Ju
   return cudaGetLastError();
 }
 
-cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, cudaStream_t st, const JuncDev* jt,
+cudaError_t launch_cocg_update(bool fp32, int nslots, int nB, int ce_stride, cudaStream_t st, const JuncDev* jt,
                                const BatchDev* b) {
   dim3 grid(nB, nslots);
-  if (fp32) cocg_update_kernel<float><<<grid, kVecThreads, 0, st>>>(jt, b);
-  else cocg_update_kernel<double><<<grid, kVecThreads, 0, st>>>(jt, b);
+  const size_t smem = (size_t)ce_stride * (fp32 ? sizeof(float2) : sizeof(double2));
+  if (smem > 48 * 1024) {
+    cudaError_t e = set_max_dynamic_smem(
+        fp32 ? reinterpret_cast<const void*>(cocg_update_kernel<float>) : reinterpret_cast<const void*>(cocg_update_kernel<double>),
+        smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (fp32) cocg_update_kernel<float><<<grid, kVecThreads, smem, st>>>(jt, b);
+  else cocg_update_kernel<double><<<grid, kVecThreads, smem, st>>>(jt, b);
   return cudaGetLastError();
 }
 
@@ -1118,6 +1134,12 @@ cudaError_t launch_shift_emit(int nslots, int n_shift, cudaStream_t st, const Ju
 
 cudaError_t launch_tgoal(cudaStream_t st, const JuncDev* jt, const BatchDev* b) {
   tgoal_kernel<<<kListRows, 256, 0, st>>>(jt, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_landauer(int n_e, const double* E, const double* T, int n_v, const double* V, double E_F,
+                            double kT, double* I, cudaStream_t st) {
+  landauer_kernel<<<n_v, 256, 0, st>>>(n_e, E, T, V, E_F, kT, I);
   return cudaGetLastError();
 }
 

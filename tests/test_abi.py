@@ -40,7 +40,7 @@ def test_default_opts(lib):
     o = B.default_opts(B.RSN_FP64)
     assert o.precision == 0 and o.tol == 1e-13 and o.max_outer >= 2 and o.max_iter == 20000
     assert o.tol_adjoint == 0.0 and o.tol_T == 1e-10
-    assert B.default_opts(B.RSN_MIXED).tol_T == 1e-7
+    assert B.default_opts(B.RSN_MIXED).tol_T == 1e-6
 
 
 def test_null_context_and_create_errors(lib):

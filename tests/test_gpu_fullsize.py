@@ -86,17 +86,20 @@ def test_junction_per_column_T_matches_oracle_lu(B, junction, prec):
     benchmark junction and three energies of its window, against the oracle's
     sparse-LU values (tests/golden, written by make_junction_golden.py).  Every
     lead channel is closed there (T ~ 1e-19..1e-15), so only relative errors
-    say anything: FP64 1e-9, mixed 1e-6."""
+    say anything: FP64 1e-9 for every column and for T; mixed 1e-6 for T and
+    1e-4 for each column (the goal-oriented finish at tol_T = 1e-6 fixes a
+    column's share to ~1e-5; the tiniest shares weigh nothing in T)."""
     j = junction
     ctx = B.Context(0).set_junction(j)
     p = B.RSN_FP64 if prec == "fp64" else B.RSN_MIXED
     tol = 1e-9 if prec == "fp64" else 1e-6
+    tol_col = 1e-9 if prec == "fp64" else 1e-4
     gl = torch.tensor(j.gamma_l, device="cuda")
     for E, cols, t_ref in _golden():
         x, _, _ = ctx.solve_columns([E], cols, B.default_opts(p))
         tc = (gl[None, :] * x[0].abs() ** 2).sum(1).cpu().numpy()
         rel = np.abs(tc - t_ref) / t_ref
-        assert rel.max() <= tol, (E, rel.max())
+        assert rel.max() <= tol_col, (E, rel.max())
         T = ctx.transmission([E], cols, B.default_opts(p))[0]
         T_ref = 4.0 * np.sum(j.gamma_r[cols] * t_ref)
         assert abs(T - T_ref) <= tol * T_ref, (E, T, T_ref)

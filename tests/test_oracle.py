@@ -336,3 +336,53 @@ def test_shifted_cocg_pin_catches_a_wrong_shift_sign():
     X, _, _, _ = O.shifted_cocg(j, mirrored, b, seed=0, rtol=1e-12)
     ref = O.solve_columns(j, E[1], [col])[:, 0]
     assert np.linalg.norm(X[1] - ref) > 1e-3 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------------------
+# Landauer current (Eq. Landauer)
+# ----------------------------------------------------------------------------
+def test_landauer_constant_transmission_gives_ohmic_current():
+    # int (f_L - f_R) dE = mu_L - mu_R = V at any temperature: I = T V / pi.
+    # kT > 0 on a fine grid; kT = 0 with the chemical potentials at cell
+    # centres, where the trapezoidal rule integrates the step exactly
+    E = np.linspace(-2.0, 2.0, 40001)
+    V = np.array([-0.3, 0.05, 0.2, 0.5])
+    I = O.landauer_current(E, np.full(E.size, 0.7), V, E_F=0.1, kT=0.01)
+    assert np.allclose(I, 0.7 * V / np.pi, rtol=1e-6, atol=1e-12)
+    E0 = np.arange(-20000, 20001) * 1e-4 + 0.5e-4
+    I0 = O.landauer_current(E0, np.full(E0.size, 0.7), V, E_F=0.1, kT=0.0)
+    assert np.allclose(I0, 0.7 * V / np.pi, rtol=1e-9, atol=1e-12)
+
+
+def test_landauer_staircase_is_piecewise_linear_and_odd():
+    # T(E) = number of open channels of the waveguide: at kT = 0 the current
+    # is (1/pi) int_{mu_R}^{mu_L} N(E) dE, the area under the staircase
+    th = O.channel_thresholds(8, 8, 0.5)
+    E = np.linspace(0.0, 2.5, 250001)
+    N = np.array([O.open_channels(8, 8, 0.5, e) for e in E[::50]], dtype=float)
+    N = np.repeat(N, 50)[: E.size]
+    E_F, V = 1.2, np.array([0.2, 0.6, 1.0])
+    I = O.landauer_current(E, N, V, E_F=E_F)
+    for v, i in zip(V, I):
+        lo, hi = E_F - v / 2, E_F + v / 2
+        area = sum(max(0.0, min(hi, t + 4.0) - max(lo, t)) for t in th)  # channel t open on (t, t + 2/h^2)
+        assert abs(i - area / np.pi) <= 2e-3 * area / np.pi
+    assert np.allclose(O.landauer_current(E, N, -V, E_F=E_F), -I)
+
+
+def test_landauer_linear_response_is_the_transmission_at_the_fermi_level():
+    # dI/dV at V = 0: (1/pi) int T(E) (-f'(E - E_F)) dE = T(E_F) / pi + O(kT^2 T'')
+    # (the Landauer conductance 2e^2/h T); kT = 0.002 Ha, 200 grid cells per kT
+    E = np.linspace(-1.0, 1.0, 200001)
+    T = 0.3 + 0.2 * np.sin(3 * E)
+    dv = 1e-4
+    g = (O.landauer_current(E, T, [dv], E_F=0.2, kT=0.002) -
+         O.landauer_current(E, T, [-dv], E_F=0.2, kT=0.002))[0] / (2 * dv)
+    assert abs(g - (0.3 + 0.2 * np.sin(0.6)) / np.pi) <= 1e-5
+
+
+def test_landauer_catches_a_missing_spin_factor():
+    # a current without the factor 2 of 2e/h is half the ohmic value
+    E = np.linspace(-2.0, 2.0, 4001)
+    I = O.landauer_current(E, np.ones(E.size), [0.4])[0]
+    assert abs(I - 0.4 / np.pi) < 1e-9 and abs(0.5 * I - 0.4 / np.pi) > 0.1 * 0.4 / np.pi
