@@ -14,8 +14,9 @@ gradient sums.
 Beside the timed steps the JSON line carries
   * ``roofline``: the COCG operator kernel timed with CUDA events in a separate
     pass over the same energies (no events inside the timed region);
-  * ``forward_T``: T(E) alone over all 4,608 right-CAP columns at two seeded
-    energies, mixed precision and FP64 on the same columns, with |dT| per energy;
+  * ``forward_T``: T(E) alone over 1,152 right-CAP columns (every 4th) at six
+    seeded energies of the window, mixed precision and FP64 on the same columns,
+    with |dT| and relative dT per energy and the window-averaged speed ratio;
   * ``parity``: T and per-column contributions of 16 golden columns at three
     energies against the oracle's sparse-LU values (tests/golden);
   * ``e2e``: the step through the public API from host buffers (potential in,
@@ -56,9 +57,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "junction_24x24x120_tc.txt")
 # DRAM bytes per algorithmic byte of the COCG operator kernel, from one ncu
 # capture of the kernel micro-benchmark (python -m paper_1401_0782_gb300.kernel_bench
 # --kind op --slots 256 --reps 3): dram__bytes_read.sum + dram__bytes_write.sum
-# over 32 B x 69,120 points x 256 systems.  None until that capture is taken
-# for the current kernel.
-OP_DRAM_PER_ALG_BYTE = None
+# = 594.3 MB over 32 B x 69,120 points x 256 systems = 566.2 MB.  Retaken
+# whenever that kernel changes.
+OP_DRAM_PER_ALG_BYTE = 594.331392 / 566.23104
 
 
 def _env_int(k, d):
@@ -589,8 +590,9 @@ def main():
     ap.add_argument("--cols-per-step", type=int, default=288,
                     help="columns per step: every k-th of the 4,608 right-CAP columns (0 = all)")
     ap.add_argument("--roofline-steps", type=int, default=2, help="steps of the event-timed roofline pass")
-    ap.add_argument("--fwd-energies", type=int, default=2, help="energies of the forward-T comparison")
-    ap.add_argument("--fwd-cols", type=int, default=0, help="columns of the forward-T comparison (0 = all 4,608)")
+    ap.add_argument("--fwd-energies", type=int, default=6, help="energies of the forward-T comparison")
+    ap.add_argument("--fwd-cols", type=int, default=1152,
+                    help="columns of the forward-T comparison, every k-th of the 4,608 (0 = all)")
     ap.add_argument("--window-energies", type=int, default=16, help="energies of the shifted-COCG window leg (0 = skip)")
     ap.add_argument("--window-cols", type=int, default=128, help="columns of the shifted-COCG window leg")
     ap.add_argument("--batch-junctions", type=int, default=64, help="junctions of the slot-pool leg (0 = skip)")
