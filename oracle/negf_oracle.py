@@ -346,7 +346,17 @@ def shifted_cocg(j, energies: Sequence[float], b: np.ndarray, seed: int = 0, rto
     pi = np.ones(nE, dtype=np.complex128)
     if bn == 0.0:
         return X, 0, pi, b.copy()
-    Hloc = local_hamiltonian(j)
+    # the seed operator A(E_s) = A_loc(E_s) - B^T diag(e_kb) B, assembled once
+    # (the same sparse products as apply_operator, without rebuilding them per step)
+    A_loc = local_system_matrix(j, Es)
+    Bp = _projector_rows(j) if j.n_proj else None
+
+    def seed_op(v):
+        y = A_loc @ v
+        if Bp is not None:
+            y = y - Bp.T @ (j.proj_ekb * (Bp @ v))
+        return y
+
     r = b.copy()
     P = np.repeat(r[None, :], nE, axis=0)  # p^sig_0 = r_0 / pi_0 = b
     pi_old = np.ones(nE, dtype=np.complex128)
@@ -356,7 +366,7 @@ def shifted_cocg(j, energies: Sequence[float], b: np.ndarray, seed: int = 0, rto
     limit = maxiter if stop_at is None else stop_at
     while k < limit:
         p = P[seed]
-        q = apply_operator(j, Es, p, Hloc)
+        q = seed_op(p)
         alpha = rho / (p @ q)
         r = r - alpha * q
         rho_new = r @ r

@@ -1,6 +1,12 @@
 import os
 import sys
 
+# the oracle's sparse LU runs single-threaded (SuperLU); threaded BLAS under it
+# only oversubscribes the cores (a 3,000-point factorisation went from 0.9 s to
+# 75 s on a loaded host), so the test processes keep BLAS to one thread
+for _k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_k, "1")
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
