@@ -95,14 +95,15 @@ typedef struct {
                            small on the Gamma_L support and a residual of tol relative to the
                            whole column fixes t_j only to ~1e-3 (tol 1e-10) or ~1e-6 (1e-13);
                            the iterate keeps converging there after its residual reaches the
-                           rounding floor.  Measured on the 24x24x120 junction: tol_T 1e-6
-                           (mixed default) leaves each t_j within ~1e-5 and T within ~1e-7 of
-                           the FP64 columns; 1e-10 (FP64 default) within ~1e-11.
+                           rounding floor.  Measured on the 24x24x120 junction against the
+                           oracle's LU: tol_T 1e-7 (mixed default) leaves T within ~1e-7 and
+                           each t_j within ~1e-4 (the tiniest shares); 3e-11 (FP64 default)
+                           within ~1e-10.
                            0 = residual criterion alone. */
 } rsn_solver_opts;
 
-/* Defaults for a precision: FP64 -> tol 1e-13, tol_T 1e-10, tol_inner 1e-6,
-   max_iter 20000; MIXED -> tol 1e-10, tol_T 1e-6, tol_inner 1e-1, max_iter 3000
+/* Defaults for a precision: FP64 -> tol 1e-13, tol_T 3e-11, tol_inner 1e-6,
+   max_iter 20000; MIXED -> tol 1e-10, tol_T 1e-7, tol_inner 1e-1, max_iter 3000
    (a system that needs more, or whose FP32 recurrence stalls, is solved again
    in FP64 from zero);
    both: tol_adjoint 0 (= tol), max_outer 64, graphs on (16 iterations per

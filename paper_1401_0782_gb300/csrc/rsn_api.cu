@@ -530,12 +530,12 @@ void rsn_default_opts(int precision, rsn_solver_opts* o) {
     o->tol = 1e-10;
     o->tol_inner = 1e-1;
     o->max_iter = 3000;  // slower systems are handed to the FP64 fallback
-    o->tol_T = 1e-6;
+    o->tol_T = 1e-7;
   } else {
     o->tol = 1e-13;
     o->tol_inner = 1e-6;
     o->max_iter = 20000;
-    o->tol_T = 1e-10;
+    o->tol_T = 3e-11;
   }
   o->tol_adjoint = 0.0;  // the adjoint systems take tol
   o->max_outer = 64;

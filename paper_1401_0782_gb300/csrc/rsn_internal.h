@@ -24,8 +24,7 @@ constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
 constexpr int kCePad = 16;
 constexpr int kMaxGraphIters = 256;
 constexpr int kMaxApplyRhs = 65535;
-constexpr int kMaxGoalChecks = 24;   // T checks of a goal phase before its iterate is kept
-constexpr int kGoalCycle = 40;       // iterations between T checks at most (or a tenfold cut of the recurrence)  // vectors per operator-application call (grid y dimension)
+constexpr int kMaxGoalChecks = 24;   // T checks of a goal phase before it ends  // vectors per operator-application call (grid y dimension)
 constexpr int kSchedThreads = 1024;
 // CTA rows of the kernels that work only on NEW / CHECK slots (zero, true
 // residual and its projections, x update): each row takes list entries

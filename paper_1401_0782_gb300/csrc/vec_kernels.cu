@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(32 * kBookWarps) book_kernel(const JuncDev* __
     b.restart[s] = 1;
     b.rrec2[s] = 0.0;
     b.state[s] = SL_CHECK;
-  } else if (nrm <= b.tol2[s] || tot >= b.max_iter || cyc >= b.cycle_cap || (b.gphase[s] && cyc >= kGoalCycle)) {
+  } else if (nrm <= b.tol2[s] || tot >= b.max_iter || cyc >= b.cycle_cap) {
     b.rrec2[s] = nrm;
     b.state[s] = b.gphase[s] ? SL_CHECKT : SL_CHECK;
   }
@@ -400,14 +400,18 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
       b.tlast[s] = tcur;
       const int gcnt = b.gcnt[s] + 1;
       b.gcnt[s] = gcnt;
-      const bool done = fabs(tcur - tl) <= b.tol_T * fabs(tcur) || gcnt >= kMaxGoalChecks ||
-                        b.total_iters[s] >= b.max_iter;
-      if (done) {
+      const bool settled = fabs(tcur - tl) <= b.tol_T * fabs(tcur);
+      const bool capped = gcnt >= kMaxGoalChecks || b.total_iters[s] >= b.max_iter;
+      if (settled || capped) {
+        // a mixed-precision system whose T partial did not settle within the cap
+        // is handed back (solved again in FP64); FP64 keeps its iterate
+        const bool back = !settled && b.handback;
         const int sy = b.sys[s];
         b.out_iters[sy] = b.total_iters[s];
         b.out_relres[sy] = b.rgoal[s];
-        b.out_status[sy] = 0;
+        b.out_status[sy] = back ? 3 : 0;
         atomicAdd(b.counters + 2, 1ull);
+        if (back) atomicAdd(b.counters + 3, 1ull);
         st = SL_DRAIN;
       } else {
         b.tol2[s] = 0.01 * b.rrec2[s];

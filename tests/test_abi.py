@@ -39,8 +39,8 @@ def test_default_opts(lib):
     assert o.precision == 1 and o.tol == 1e-10 and o.tol_inner == 1e-1 and o.use_graph == 1
     o = B.default_opts(B.RSN_FP64)
     assert o.precision == 0 and o.tol == 1e-13 and o.max_outer >= 2 and o.max_iter == 20000
-    assert o.tol_adjoint == 0.0 and o.tol_T == 1e-10
-    assert B.default_opts(B.RSN_MIXED).tol_T == 1e-6
+    assert o.tol_adjoint == 0.0 and o.tol_T == 3e-11
+    assert B.default_opts(B.RSN_MIXED).tol_T == 1e-7
 
 
 def test_null_context_and_create_errors(lib):

@@ -65,6 +65,35 @@ def test_apply_matches_oracle_operator(B, name, tiling):
     ctx.close()
 
 
+@pytest.mark.parametrize("fn", ["rsn_apply", "rsn_apply_noalloc"])
+@pytest.mark.parametrize("tiling", [(0, 0, 0), (0, 11, -1), (0, 13, -2), (0, 17, -3)])
+def test_apply_with_unaligned_vectors(B, fn, tiling):
+    # vectors 8 bytes off a 16-byte boundary cannot be bulk-copied: the apply
+    # entry points fall back to a register tiling that fits the CTA limits
+    j = JUNCTIONS["bench_plane_R4"]()
+    ctx = B.Context(0).set_junction(j)
+    ctx.set_tiling(*tiling)
+    rng = np.random.default_rng(2)
+    E = np.array([0.2, 0.4])
+    xr = rng.standard_normal((E.size, j.N)) + 1j * rng.standard_normal((E.size, j.N))
+    xb = torch.zeros(E.size * j.N + 1, dtype=torch.complex64, device="cuda")
+    yb = torch.zeros_like(xb)
+    x = xb[1:]
+    x.copy_(torch.tensor(xr.ravel(), dtype=torch.complex64))
+    y = yb[1:]
+    assert x.data_ptr() % 16 == 8 and y.data_ptr() % 16 == 8
+    if fn == "rsn_apply_noalloc":
+        ctx.apply(E, torch.zeros((E.size, j.N), dtype=torch.complex64, device="cuda"), B.RSN_MIXED)  # upload
+    rc = getattr(ctx.lib, fn)(ctx.h, B.RSN_MIXED, int(E.size), E.ctypes.data, x.data_ptr(), y.data_ptr())
+    assert rc == B.RSN_OK, ctx.lib.rsn_last_error(ctx.h).decode()
+    torch.cuda.synchronize()
+    yh = y.cpu().numpy().reshape(E.size, j.N)
+    xh = x.cpu().numpy().reshape(E.size, j.N).astype(np.complex128)
+    ref = np.stack([O.apply_operator(j, e, xh[k]) for k, e in enumerate(E)])
+    assert np.abs(yh - ref).max() <= 2e-6 * np.abs(ref).max()
+    ctx.close()
+
+
 def test_solve_columns_fp64_matches_lu(B):
     j = JUNCTIONS["junction_R4"]()
     E = [0.17, 0.23]
