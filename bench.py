@@ -57,9 +57,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "junction_24x24x120_tc.txt")
 # DRAM bytes per algorithmic byte of the COCG operator kernel, from one ncu
 # capture of the kernel micro-benchmark (python -m paper_1401_0782_gb300.kernel_bench
 # --kind op --slots 256 --reps 3): dram__bytes_read.sum + dram__bytes_write.sum
-# = 594.3 MB over 32 B x 69,120 points x 256 systems = 566.2 MB.  Retaken
+# = 593.3 MB over 32 B x 69,120 points x 256 systems = 566.2 MB.  Retaken
 # whenever that kernel changes.
-OP_DRAM_PER_ALG_BYTE = 594.331392 / 566.23104
+OP_DRAM_PER_ALG_BYTE = 593.25952 / 566.23104
 
 
 def _env_int(k, d):
@@ -410,7 +410,7 @@ def run_ours(args):
             },
             "passes_per_iteration": passes_per_iteration(j),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "steps": len(e2e_ks), "energies": "those of the timed steps",
+                    "steps": len(e2e_ks), "energies": "those of the timed steps (cycled to at least five)",
                     "per_step": "set_potential (host V_loc) + transmission_vjp with host T and dV"},
             "gpu_launches": int(launches),
             "krylov_iters_per_solve": iters / float(args.steps * 2 * n_cols),
