@@ -480,6 +480,35 @@ def run_ours(args):
             "plain_fp64_fallbacks": ss["fp64_fallbacks"],
         }
 
+    # ---- block COCG: the columns of one energy share one Krylov space ------
+    if rank == 0 and not args.no_fp64 and args.block_cols > 0:
+        E_blk = np.linspace(E_LO, E_HI, N_ENERGIES)[[37, 101]]
+        kcols = all_cols[:: max(1, all_cols.size // args.block_cols)]
+        om = B.default_opts(B.RSN_MIXED, deadline_ms=args.deadline * 1e3)
+        leg = {"sample": f"{kcols.size} right-CAP columns x energies {E_blk.round(5).tolist()}; forward T, host-timed "
+                         "library calls, both paths on the same systems"}
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Tm = ctx.transmission(E_blk, kcols, om)
+            tm = time.perf_counter() - t0
+            sm = ctx.last_stats()
+            n = E_blk.size * kcols.size
+            leg["plain_mixed_solves_per_s"] = n / tm
+            leg["plain_mixed_iters_per_solve"] = sm["krylov_iters"] / n
+            for blk in (16, 8):
+                t0 = time.perf_counter()
+                Tb, tc, its = ctx.transmission_block(E_blk, kcols, block=blk, opts=om, return_cols=True)
+                tb = time.perf_counter() - t0
+                sb = ctx.last_stats()
+                leg[f"block{blk}"] = {"solves_per_s": n / tb, "over_plain_mixed": tm / tb,
+                                      "operator_applications_per_column": float(its.mean()),
+                                      "columns_handed_to_plain_solver": int(sb["fp64_fallbacks"]),
+                                      "max_rel_dT_vs_plain_mixed": float(np.max(np.abs(Tb - Tm) / np.abs(Tm)))}
+        except B.RsnError as exc:
+            leg["error"] = str(exc)
+        result["block_T"] = leg
+
     # ---- many uneven junctions in one slot pool ----------------------------
     if rank == 0 and args.batch_junctions > 0:
         bj = P.batched_junctions()[: args.batch_junctions]
@@ -598,6 +627,7 @@ def main():
                     help="columns of the forward-T comparison, every k-th of the 4,608 (0 = all)")
     ap.add_argument("--window-energies", type=int, default=16, help="energies of the shifted-COCG window leg (0 = skip)")
     ap.add_argument("--window-cols", type=int, default=128, help="columns of the shifted-COCG window leg")
+    ap.add_argument("--block-cols", type=int, default=288, help="columns of the block-COCG leg (0 = skip)")
     ap.add_argument("--batch-junctions", type=int, default=64, help="junctions of the slot-pool leg (0 = skip)")
     ap.add_argument("--batch-energies", type=int, default=8, help="energies per junction in the slot-pool leg")
     ap.add_argument("--batch-col-stride", type=int, default=256, help="every k-th right-CAP column in the pool leg")

@@ -220,6 +220,59 @@ rsn_status rsn_transmission_shifted(rsn_ctx* ctx, int n_e, const double* E, int 
                                     const int32_t* cols, const rsn_solver_opts* opts, double* T,
                                     int32_t* iters);
 
+/* Block COCG: the columns of one energy, in blocks of `block` (4, 8 or 16)
+   columns, each block sharing ONE block Krylov space of A(E) (A = A^T by Eq.
+   complex-sym, so block CG carries over with the unconjugated bilinear form;
+   the right-hand sides e_j of a block see each other's search directions).
+   The paper solves one Green's-function column at a time; sharing the space
+   across the right-hand sides of one energy is this library's: a block of 16
+   reduces its unit columns' residuals 1e4-fold in about a third of the plain
+   recurrence's iterations.
+   Each block runs FP64 outer steps: the true residual R = b - A X, then an
+   inner block COCG in complex FP32 on A D = R (columns scaled to unit norm)
+   whose residual block is kept orthonormal (R_k = Q_k xi_k, Cholesky QR, so
+   columns that converge at different rates never make the block singular),
+   until every column's residual fell by tol_inner (0: 1e-4); then X += D.
+   A column is done when ||b - A x|| <= tol ||b|| and, if opts->tol_T > 0,
+   the change of its T partial t = sum_{i in L} Gamma_L,i |x(i)|^2 made by the
+   last outer step, times ten times that step's residual reduction, is at most
+   tol_T t; a block is done when all its columns are.  A block whose inner
+   solve breaks down or runs long -- the first past min(max_iter, 1000)
+   iterations, a restart past twice the first one's count: its FP32 block
+   recurrence lost its orthogonality --, that stalls for three outer steps or
+   reaches max_outer keeps its last FP64 iterate and hands its columns to the
+   plain slot-pool solver of rsn_solve_columns (warm-started there, with that
+   solver's FP64 re-solve of stalled systems), so every column meets the same
+   targets.  opts->precision must be RSN_MIXED; deadline_ms as
+   rsn_solve_columns.  cols must be distinct; a short last block of an energy
+   is padded with other grid points whose solutions are dropped.
+   x_dev: device, [n_e][n_cols][N] complex128 (as rsn_solve_columns);
+   t_cols (host, n_e*n_cols, may be NULL): each column's T partial t;
+   iters (host, may be NULL): operator applications of the column's block
+   (inner iterations plus FP64 residuals) plus the plain solver's iterations
+   of a handed-back column; < 0 if the column did not converge;
+   relres (host, may be NULL): final ||b - A x|| / ||b||.
+   Errors: RSN_EINVAL (block not 4/8/16, precision, tol_inner outside (0, 1),
+   repeated columns, a grid of fewer than 2 block points, as rsn_solve_columns);
+   RSN_ENOCONV (a handed-back column failed in the plain solver too; outputs
+   still written); RSN_ETIMEOUT; RSN_ENOMEM / RSN_ECUDA.
+   rsn_last_stats: krylov_iters = block operator applications summed over the
+   columns plus the plain solver's iterations, fp64_fallbacks = the columns
+   handed to the plain solver. */
+rsn_status rsn_solve_columns_block(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                                   const int32_t* cols, int block, double tol_inner,
+                                   const rsn_solver_opts* opts, void* x_dev, double* t_cols,
+                                   int32_t* iters, double* relres);
+
+/* T(E) by Eq. T-realspace from block COCG columns (as rsn_solve_columns_block,
+   without storing the columns): T[e] = 4 sum_c Gamma_R[cols[c]] t_{e,c}, FP64
+   in a fixed order.  T: host, n_e doubles; t_cols, iters: as above (may be
+   NULL).  Errors: as rsn_solve_columns_block. */
+rsn_status rsn_transmission_block(rsn_ctx* ctx, int n_e, const double* E, int n_cols,
+                                  const int32_t* cols, int block, double tol_inner,
+                                  const rsn_solver_opts* opts, double* T, double* t_cols,
+                                  int32_t* iters);
+
 /* T(E) as rsn_transmission, keeping the forward columns: x_dev (device,
    [n_e][n_cols][N] complex128, caller-owned) receives x_{e,c} = G(E[e]) e_{cols[c]}
    so that a later rsn_transmission_vjp_reuse needs only the adjoint solves.

@@ -43,6 +43,11 @@ _SIGS = {
                                              ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_transmission_shifted": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
                                             ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "rsn_solve_columns_block": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int,
+                                           ct.c_double, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                           ct.c_void_p]),
+    "rsn_transmission_block": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int,
+                                          ct.c_double, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
     "rsn_transmission_keep": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p,
                                          ct.c_void_p, ct.c_void_p]),
     "rsn_transmission_vjp_reuse": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_void_p,
@@ -248,6 +253,48 @@ class Context:
                     self.lib.rsn_transmission_shifted(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
                                                       ct.byref(opts), _ptr(T), _ptr(iters)))
         return (T, iters.reshape(E.size, cols.size)) if return_iters else T
+
+    def solve_columns_block(self, E: Sequence[float], cols: Sequence[int], block: int = 16,
+                            tol_inner: float = 0.0, opts: Optional[SolverOpts] = None,
+                            raise_on_noconv: bool = True):
+        """Columns by block COCG (blocks of ``block`` columns of one energy share one
+        Krylov space; FP32 block recurrence under FP64 refinement): (CUDA complex128
+        tensor (n_e, n_cols, N), T partials (n_e, n_cols), operator applications,
+        relative residuals)."""
+        torch = _torch()
+        opts = opts or default_opts(RSN_MIXED)
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        x = torch.empty((E.size, cols.size, self.N), dtype=torch.complex128, device=f"cuda:{self.device}")
+        tc = np.zeros(E.size * cols.size, np.float64)
+        iters = np.zeros(E.size * cols.size, np.int32)
+        relres = np.zeros(E.size * cols.size, np.float64)
+        rc = self.lib.rsn_solve_columns_block(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols), int(block),
+                                              float(tol_inner), ct.byref(opts), x.data_ptr(), _ptr(tc),
+                                              _ptr(iters), _ptr(relres))
+        if rc != RSN_OK and (raise_on_noconv or rc not in (RSN_ENOCONV, RSN_ETIMEOUT)):
+            self._check("rsn_solve_columns_block", rc)
+        sh = (E.size, cols.size)
+        return x, tc.reshape(sh), iters.reshape(sh), relres.reshape(sh)
+
+    def transmission_block(self, E: Sequence[float], cols: Optional[Sequence[int]] = None, block: int = 16,
+                           tol_inner: float = 0.0, opts: Optional[SolverOpts] = None, return_cols: bool = False):
+        """T(E) from block COCG columns; with ``return_cols`` also the per-column T
+        partials and operator applications, each (n_e, n_cols)."""
+        opts = opts or default_opts(RSN_MIXED)
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        if cols is None:
+            cols = self.junction.right_columns()
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        T = np.zeros(E.size, np.float64)
+        tc = np.zeros(E.size * cols.size, np.float64)
+        iters = np.zeros(E.size * cols.size, np.int32)
+        self._check("rsn_transmission_block",
+                    self.lib.rsn_transmission_block(self.h, int(E.size), _ptr(E), int(cols.size), _ptr(cols),
+                                                    int(block), float(tol_inner), ct.byref(opts), _ptr(T),
+                                                    _ptr(tc), _ptr(iters)))
+        sh = (E.size, cols.size)
+        return (T, tc.reshape(sh), iters.reshape(sh)) if return_cols else T
 
     def transmission(self, E: Sequence[float], cols: Optional[Sequence[int]] = None,
                      opts: Optional[SolverOpts] = None) -> np.ndarray:

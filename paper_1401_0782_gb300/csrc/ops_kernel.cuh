@@ -568,7 +568,7 @@ op_kernel_tma(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, c
     if (s_bad) {
       // a copy never arrived: report, let in-flight copies land (bounded), leave
       if (tid == 0) {
-        atomicExch(b.sched + 2, 1);
+        if (b.sched) atomicExch(b.sched + 2, 1);
         for (int f = 0; f < kStages; ++f) {
           const int zq = zl + f;
           if (zq < ze) mbar_wait(bars + (zq - zb) % kStages, (uint32_t)(((zq - zb) / kStages) & 1));

@@ -216,7 +216,7 @@ op_pair_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp, 
         if (s_bad) {
           // a copy never arrived: report, let in-flight copies land (bounded), leave
           if (tid == 0) {
-            atomicExch(b.sched + 2, 1);
+            if (b.sched) atomicExch(b.sched + 2, 1);
             for (int f = 0; f < kPairStages; ++f) {
               const int zq2 = zl + f;
               if (zq2 < ze) mbar_wait(bars + (zq2 - zb) % kPairStages, (uint32_t)(((zq2 - zb) / kPairStages) & 1));
@@ -461,7 +461,7 @@ op_plane_kernel(const JuncDev* __restrict__ jt, const BatchDev* __restrict__ bp,
         __syncthreads();
         if (s_bad) {
           if (tid == 0) {
-            atomicExch(b.sched + 2, 1);
+            if (b.sched) atomicExch(b.sched + 2, 1);
             for (int f = 0; f < kPairStages; ++f) {
               const int zq2 = zl + f;
               if (zq2 < ze) mbar_wait(bars + (zq2 - zb) % kPairStages, (uint32_t)(((zq2 - zb) / kPairStages) & 1));

@@ -75,7 +75,8 @@ struct Workspace {
   DevBuf Xslot, r, p0, p1, q, d;
   DevBuf state, sys, junc, E, col, voff, xo, xfo, iters, total_iters, cyc_iters, n_upd, restart, stall, warm, rho_cur, beta_cur;
   DevBuf bnorm2, sigma, rlast2, rrec2, tol2;
-  DevBuf rho0, nrm0, t0, tlast, gcnt, gphase, tgoal, rgoal, rho, nrm, mu, c_r, c_p, c_x, sched, counters, lst, lst_n, fslot, c_e;
+  DevBuf rho0, nrm0, t0, tlast, gcnt, gphase, tgoal, rgoal, rho, nrm, mu, c_r, c_p, c_x, sched, counters, lst, lst_n,
+      inlist, fslot, c_e;
   int generation = 0;
 };
 
@@ -115,6 +116,14 @@ struct PoolSpec {
   const JuncDev* jr = nullptr;            // device: K JuncDev with the residual tilings
 };
 
+// Buffers of the block COCG solver (rsn_*_block): FP32 block vectors W, P, AP,
+// D and the FP64 iterate / residual of every member of a wave of blocks, the
+// b x b state of each block, and the apply lists of the active members.
+struct BlkBufs {
+  DevBuf W, P, AP, D, X, R, part, xi, QQ, xi0n, alpha, axi, tinv, tinv64, beta, flag, its, rpart, rn, tt, blist, col;
+  DevBuf vE, vjunc, voff, cbuf, dev, bdev, jd, t_all, gr_cols, Td, stat, icap;
+};
+
 struct GraphKey {
   int fp32, slots, iters, generation, proj, timing, n_shift, nT;
   bool operator<(const GraphKey& o) const {
@@ -129,7 +138,8 @@ struct rsn_ctx {
   int device = 0;
   cudaStream_t user_stream = nullptr;
   cudaStream_t st = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaStream_t st2 = nullptr;  // second stream: the true-residual path beside the COCG step
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr, ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 
   bool has_grid = false, has_v = false, has_cap = false;
@@ -154,6 +164,7 @@ struct rsn_ctx {
 
   Workspace ws;
   CallBufs cb;
+  BlkBufs bb;
   DevBuf bd;  // device BatchDev: [0] streaming solver, [1] rsn_apply
   std::map<GraphKey, cudaGraphExec_t> graphs;
   int* sched_host = nullptr;  // pinned mirror of BatchDev::sched
@@ -568,6 +579,9 @@ rsn_status rsn_create(rsn_ctx** out, int device, void* cuda_stream) {
   c->device = device;
   c->user_stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
@@ -586,6 +600,7 @@ rsn_status rsn_destroy(rsn_ctx* c) {
   if (!c) return RSN_OK;
   cudaSetDevice(c->device);
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->st2) cudaStreamSynchronize(c->st2);
   clear_graphs(c);
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   if (c->sched_host) cudaFreeHost(c->sched_host);
@@ -594,6 +609,9 @@ rsn_status rsn_destroy(rsn_ctx* c) {
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->t0) cudaEventDestroy(c->t0);
   if (c->t1) cudaEventDestroy(c->t1);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->st2) cudaStreamDestroy(c->st2);
   if (c->st) cudaStreamDestroy(c->st);
   delete c;
   return RSN_OK;
@@ -817,6 +835,8 @@ static rsn_status ensure_ws(rsn_ctx* c, bool fp32, int S, const PoolSpec* pool =
   RSN_CUDA(c, w.counters.ensure(4 * sizeof(unsigned long long)));
   RSN_CUDA(c, w.lst.ensure(si));
   RSN_CUDA(c, w.lst_n.ensure(sizeof(int)));
+  RSN_CUDA(c, w.inlist.ensure(si));
+  RSN_CUDA(c, cudaMemset(w.inlist.p, 0, si));
   RSN_CUDA(c, w.fslot.ensure(si));
   std::vector<long long> hvo(S);
   for (int s = 0; s < S; ++s) hvo[s] = (long long)s * N;
@@ -938,6 +958,7 @@ static BatchDev slot_batch(rsn_ctx* c, int S, const rsn_solver_opts* o) {
   b.counters = w.counters.as<unsigned long long>();
   b.lst = w.lst.as<int>();
   b.lst_n = w.lst_n.as<int>();
+  b.inlist = w.inlist.as<int>();
   b.fslot = w.fslot.as<int>();
   b.c_e = w.c_e.p;
   b.ce_stride = std::max(1, c->ws.n_proj) + kCePad;
@@ -1090,25 +1111,54 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
     RSN_CUDA(c, cudaEventCreate(&e));
     c->tev.push_back(e);
   }
+  // One iteration: the true-residual path of the NEW / CHECK / goal-check slots
+  // (list, zero, projections of x, FP64 residual, x update, goal check) runs on
+  // the second stream beside the COCG step of the ACTIVE slots (projections of
+  // r, operator, update, bookkeeping); both touch disjoint slots.  The
+  // scheduler then joins them: finished systems leave, checked systems resume,
+  // free slots take queued systems for the next iteration.
+  // Shifted systems keep one stream: their per-iteration shift step must see
+  // exactly the slots that did a COCG iteration, so the scheduler runs first.
+  cudaStream_t st2 = sh ? st : c->st2;
   auto body = [&](int iters, bool capturing) -> cudaError_t {
     // inside stream capture an event record must be an external node to be timeable
     const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    for (int it = 0; it < iters; ++it) {
-      cudaError_t e;
-      if ((e = launch_list(st, bdev)) != cudaSuccess) return e;
-      if ((e = launch_zero(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
-      if (sh && (e = launch_shift_init(sh->nT, st, jr, bdev)) != cudaSuccess) return e;
-      if (proj && (e = launch_project(1, fp32, KL, n_groups, max_np, st, jr, bdev, nullptr, w.c_x.p, multi)) !=
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.sched.as<int>() + 3 + kMaxGraphIters, 0, iters * sizeof(int), st)) != cudaSuccess)
+      return e;
+    auto residual_path = [&]() -> cudaError_t {
+      cudaError_t e2;
+      if ((e2 = launch_list(st2, bdev)) != cudaSuccess) return e2;
+      if ((e2 = launch_zero(fp32, KL, nB, st2, jr, bdev)) != cudaSuccess) return e2;
+      if (sh && (e2 = launch_shift_init(sh->nT, st2, jr, bdev)) != cudaSuccess) return e2;
+      if (proj && (e2 = launch_project(1, fp32, KL, n_groups, max_np, st2, jr, bdev, nullptr, w.c_x.p, multi)) !=
                       cudaSuccess)
-        return e;
-      if ((e = launch_op(OP_RESID, fp32, R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st, jr, bdev,
-                         nullptr, nullptr, nullptr)) != cudaSuccess)
-        return e;
-      if ((e = launch_x_update(fp32, KL, nB, st, jr, bdev)) != cudaSuccess) return e;
-      if (goal && (e = launch_tgoal(st, jr, bdev)) != cudaSuccess) return e;
-      if ((e = launch_sched(S, it, st, jr, bdev)) != cudaSuccess) return e;
-      if ((e = launch_emit(S, st, jr, bdev)) != cudaSuccess) return e;
-      if (sh && (e = launch_shift_emit(S, ns, st, jr, bdev)) != cudaSuccess) return e;
+        return e2;
+      if ((e2 = launch_op(OP_RESID, fp32, R, cfg.resid.ppt, gr, cfg.resid.threads, cfg.resid.smem, st2, jr, bdev,
+                          nullptr, nullptr, nullptr)) != cudaSuccess)
+        return e2;
+      if ((e2 = launch_x_update(fp32, KL, nB, st2, jr, bdev)) != cudaSuccess) return e2;
+      if (goal && (e2 = launch_tgoal(st2, jr, bdev)) != cudaSuccess) return e2;
+      return cudaSuccess;
+    };
+    auto schedule = [&](int it) -> cudaError_t {
+      cudaError_t e2;
+      if ((e2 = launch_sched(S, it, st, jr, bdev)) != cudaSuccess) return e2;
+      if ((e2 = launch_emit(S, st, jr, bdev)) != cudaSuccess) return e2;
+      if (sh && (e2 = launch_shift_emit(S, ns, st, jr, bdev)) != cudaSuccess) return e2;
+      return cudaSuccess;
+    };
+    for (int it = 0; it < iters; ++it) {
+      if (sh) {
+        if ((e = residual_path()) != cudaSuccess) return e;
+        if ((e = schedule(it)) != cudaSuccess) return e;
+      } else {
+        if ((e = cudaEventRecord(c->ev_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st2, c->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = residual_path()) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_join, st2)) != cudaSuccess) return e;
+      }
+      // COCG step of the ACTIVE slots (main stream)
       if (proj && (e = launch_project(0, fp32, S, n_groups, max_np, st, ji, bdev, nullptr, w.c_r.p, multi)) !=
                       cudaSuccess)
         return e;
@@ -1128,6 +1178,11 @@ static rsn_status run_stream(rsn_ctx* c, const rsn_solver_opts* o, const StreamI
       if (timing && (e = cudaEventRecordWithFlags(c->tev[4 * it + 2], st, evf)) != cudaSuccess) return e;
       if ((e = launch_book(S, it, st, ji, bdev)) != cudaSuccess) return e;
       if (sh && (e = launch_shift_update(S, sh->nT, ns, st, ji, bdev)) != cudaSuccess) return e;
+      if (!sh) {
+        // join: the scheduler sees both paths of this iteration
+        if ((e = cudaStreamWaitEvent(st, c->ev_join, 0)) != cudaSuccess) return e;
+        if ((e = schedule(it)) != cudaSuccess) return e;
+      }
     }
     return cudaSuccess;
   };
@@ -1587,6 +1642,512 @@ rsn_status rsn_transmission_vjp(rsn_ctx* c, int n_e, const double* E, int n_cols
   if (!c) return RSN_EINVAL;
   if (!dV) RSN_FAIL(c, RSN_EINVAL, "dV is NULL");
   return transmission_impl(c, n_e, E, n_cols, cols, o, T_bar, dV, dV_is_device, T);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Block COCG: the columns of one energy in blocks of B share one block Krylov
+// space.  Each block runs FP64 outer steps (defect correction):
+//   R = b - A X (FP64), ||r_j||, t_j = sum_L Gamma_L |x_j|^2
+//   column j is done when ||r_j|| <= tol and (tol_T > 0) the change of t_j made
+//   by the last correction, scaled by ten times that step's residual
+//   reduction, is at most tol_T t_j (the t_j error of the new iterate shrinks
+//   with its residual)
+//   A D = R / ||R|| column-wise by the FP32 block recurrence (block_kernels.cu)
+//   until every column's recurrence residual fell by tol_inner
+//   X += ||R|| D
+// Blocks finish independently; the kernels of a step run over the listed
+// (active) blocks only.
+// ---------------------------------------------------------------------------
+namespace {
+struct BlkRun {
+  int B = 0, nbw = 0, S = 0;
+  std::vector<int> act;  // active blocks (wave-local)
+};
+}  // namespace
+
+// Upload the block list and the apply lists (members of the listed blocks).
+static rsn_status blk_set_lists(rsn_ctx* c, const BlkRun& br, const std::vector<int>& list,
+                                const std::vector<double>& memE) {
+  BlkBufs& q = c->bb;
+  const int B = br.B;
+  const int nm = (int)list.size() * B;
+  std::vector<long long> vo(std::max(1, nm));
+  std::vector<double> ve(std::max(1, nm));
+  for (size_t u = 0; u < list.size(); ++u)
+    for (int a = 0; a < B; ++a) {
+      const int v = list[u] * B + a;
+      vo[u * B + a] = (long long)v * c->N;
+      ve[u * B + a] = memE[v];
+    }
+  if (!list.empty()) {
+    RSN_CUDA(c, cudaMemcpyAsync(q.blist.p, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    RSN_CUDA(c, cudaMemcpyAsync(q.voff.p, vo.data(), nm * sizeof(long long), cudaMemcpyHostToDevice, c->st));
+    RSN_CUDA(c, cudaMemcpyAsync(q.vE.p, ve.data(), nm * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  }
+  BatchDev b;
+  memset(&b, 0, sizeof(b));
+  b.nslots = nm;
+  b.junc = q.vjunc.as<int>();
+  b.E = q.vE.as<double>();
+  b.voff = q.voff.as<long long>();
+  b.pstride = c->n_proj;
+  b.sched = q.stat.as<int>();  // [2]: an operator kernel's bounded wait gave up
+  RSN_CUDA(c, cudaMemcpyAsync(q.bdev.p, &b, sizeof(b), cudaMemcpyHostToDevice, c->st));
+  // pageable sources: the copies above are staged before they return
+  return RSN_OK;
+}
+
+// y = A(E) x over the listed members (projections first, then the operator)
+static rsn_status blk_apply(rsn_ctx* c, const Tiling& t, const JuncDev* jt, bool fp32, int nm, const void* x,
+                            void* y) {
+  BlkBufs& q = c->bb;
+  const BatchDev* bd = q.bdev.as<BatchDev>();
+  if (c->n_proj > 0)
+    RSN_CUDA(c, launch_project(2, fp32, nm, c->n_groups, c->max_np, c->st, jt, bd, x, q.cbuf.p));
+  RSN_CUDA(c, launch_inner(c, t, OP_APPLY, fp32, nm, c->st, jt, bd, x, y, q.cbuf.p));
+  c->st_launches += c->n_proj > 0 ? 2 : 1;
+  return RSN_OK;
+}
+
+static rsn_status block_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols, int B,
+                             double tol_in, const rsn_solver_opts* o, double2* x_out, double* t_out, double* T,
+                             int32_t* iters, double* relres) {
+  rsn_status rs = commit_setup(c);
+  if (rs != RSN_OK) return rs;
+  if ((rs = check_solve_args(c, n_e, E, n_cols, cols, o)) != RSN_OK) return rs;
+  if (B != 4 && B != 8 && B != 16) RSN_FAIL(c, RSN_EINVAL, "block = %d: must be 4, 8 or 16", B);
+  if (o->precision != RSN_MIXED)
+    RSN_FAIL(c, RSN_EINVAL, "the block recurrence runs in complex FP32 under FP64 refinement: precision must be RSN_MIXED");
+  if (tol_in == 0.0) tol_in = 1e-4;
+  if (!(tol_in > 0.0 && tol_in < 1.0)) RSN_FAIL(c, RSN_EINVAL, "tol_inner must lie in (0, 1) (0: default 1e-4)");
+  const long long N = c->N;
+  if (N < 2 * B) RSN_FAIL(c, RSN_EINVAL, "grid of %lld points is too small for blocks of %d", N, B);
+  {
+    std::vector<int32_t> sc(cols, cols + n_cols);
+    std::sort(sc.begin(), sc.end());
+    for (int k = 1; k < n_cols; ++k)
+      if (sc[k] == sc[k - 1]) RSN_FAIL(c, RSN_EINVAL, "column %d appears twice (a block needs distinct columns)", sc[k]);
+  }
+  if ((rs = enter(c)) != RSN_OK) return rs;
+  reset_stats(c);
+  BlkBufs& q = c->bb;
+  const auto t_start = std::chrono::steady_clock::now();
+  RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
+  // padding members of a short last block: grid points outside the column set
+  std::vector<int> pad;
+  {
+    std::vector<int32_t> sc(cols, cols + n_cols);
+    std::sort(sc.begin(), sc.end());
+    for (long long i = 0; i < N && (int)pad.size() < B; ++i)
+      if (!std::binary_search(sc.begin(), sc.end(), (int32_t)i)) pad.push_back((int)i);
+    if ((int)pad.size() < (B - n_cols % B) % B) {
+      leave(c);
+      RSN_FAIL(c, RSN_EINVAL, "too few grid points outside the column set to pad the last block");
+    }
+  }
+  const int nbe = (n_cols + B - 1) / B;  // blocks per energy
+  const long long nb = (long long)n_e * nbe;
+  std::vector<double> t_host((size_t)std::max(1, n_e) * std::max(1, n_cols), 0.0);
+  rsn_status worst = RSN_OK;
+  long long n_fail = 0, n_brk = 0, n_late = 0, n_hand = 0;
+  const size_t per_member = (size_t)N * (4 * sizeof(float2) + 2 * sizeof(double2)) + 4096;
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  // members per wave: within memory and within a launch's grid.y (one CTA row per member)
+  const long long cap = std::max<long long>(
+      1, std::min<long long>(kMaxApplyRhs / B, (long long)(0.5 * (double)fr / ((double)per_member * B))));
+  for (long long b0 = 0; b0 < nb; b0 += cap) {
+    BlkRun br;
+    br.B = B;
+    br.nbw = (int)std::min<long long>(cap, nb - b0);
+    br.S = br.nbw * B;
+    const int nbw = br.nbw, S = br.S;
+    // members: E, column, real (output index) or padding (-1)
+    std::vector<double> memE(S);
+    std::vector<int> memCol(S);
+    std::vector<long long> memOut(S);
+    for (int k = 0; k < nbw; ++k) {
+      const long long gb = b0 + k;
+      const int e = (int)(gb / nbe), cb = (int)(gb % nbe);
+      int np = 0;
+      for (int a = 0; a < B; ++a) {
+        const int kc = cb * B + a;
+        const int v = k * B + a;
+        memE[v] = E[e];
+        if (kc < n_cols) {
+          memCol[v] = cols[kc];
+          memOut[v] = (long long)e * n_cols + kc;
+        } else {
+          memCol[v] = pad[np++];
+          memOut[v] = -1;
+        }
+      }
+    }
+    // buffers
+    const size_t vb32 = (size_t)S * N * sizeof(float2), vb64 = (size_t)S * N * sizeof(double2);
+    RSN_CUDA(c, q.W.ensure(vb32));
+    RSN_CUDA(c, q.P.ensure(vb32));
+    RSN_CUDA(c, q.AP.ensure(vb32));
+    RSN_CUDA(c, q.D.ensure(vb32));
+    RSN_CUDA(c, q.X.ensure(vb64));
+    RSN_CUDA(c, q.R.ensure(vb64));
+    int nchunk = std::max(1, std::min(64, (4 * 152 + nbw - 1) / nbw));
+    long long chunk_pts = (N + nchunk - 1) / nchunk;
+    chunk_pts = (chunk_pts + kBlkTile - 1) / kBlkTile * kBlkTile;
+    nchunk = (int)((N + chunk_pts - 1) / chunk_pts);
+    int nchunkR = std::max(1, std::min(32, (8 * 152 + S - 1) / S));
+    long long chunkR_pts = (N + nchunkR - 1) / nchunkR;
+    nchunkR = (int)((N + chunkR_pts - 1) / chunkR_pts);
+    const size_t bb2 = (size_t)nbw * B * B;
+    RSN_CUDA(c, q.part.ensure((size_t)nbw * nchunk * 2 * B * B * sizeof(double2)));
+    RSN_CUDA(c, q.xi.ensure(bb2 * sizeof(double2)));
+    RSN_CUDA(c, q.QQ.ensure(bb2 * sizeof(double2)));
+    RSN_CUDA(c, q.xi0n.ensure((size_t)S * sizeof(double)));
+    RSN_CUDA(c, q.alpha.ensure(bb2 * sizeof(float2)));
+    RSN_CUDA(c, q.axi.ensure(bb2 * sizeof(float2)));
+    RSN_CUDA(c, q.tinv.ensure(bb2 * sizeof(float2)));
+    RSN_CUDA(c, q.tinv64.ensure(bb2 * sizeof(double2)));
+    RSN_CUDA(c, q.beta.ensure(bb2 * sizeof(float2)));
+    RSN_CUDA(c, q.flag.ensure((size_t)nbw * sizeof(int)));
+    RSN_CUDA(c, q.its.ensure((size_t)nbw * sizeof(int)));
+    RSN_CUDA(c, q.rpart.ensure((size_t)S * nchunkR * 2 * sizeof(double)));
+    RSN_CUDA(c, q.rn.ensure((size_t)S * sizeof(double)));
+    RSN_CUDA(c, q.tt.ensure((size_t)S * sizeof(double)));
+    RSN_CUDA(c, q.blist.ensure((size_t)nbw * sizeof(int)));
+    RSN_CUDA(c, q.col.ensure((size_t)S * sizeof(int)));
+    RSN_CUDA(c, q.vE.ensure((size_t)S * sizeof(double)));
+    RSN_CUDA(c, q.vjunc.ensure((size_t)S * sizeof(int)));
+    RSN_CUDA(c, q.voff.ensure((size_t)S * sizeof(long long)));
+    RSN_CUDA(c, q.cbuf.ensure((size_t)S * std::max(1, c->n_proj) * sizeof(double2)));
+    RSN_CUDA(c, q.dev.ensure(sizeof(BlkDev)));
+    RSN_CUDA(c, q.bdev.ensure(sizeof(BatchDev)));
+    RSN_CUDA(c, q.jd.ensure(2 * sizeof(JuncDev)));
+    RSN_CUDA(c, q.stat.ensure(4 * sizeof(int)));
+    RSN_CUDA(c, cudaMemsetAsync(q.stat.p, 0, 4 * sizeof(int), c->st));
+    RSN_CUDA(c, cudaMemsetAsync(q.vjunc.p, 0, (size_t)S * sizeof(int), c->st));
+    RSN_CUDA(c, cudaMemsetAsync(q.X.p, 0, vb64, c->st));
+    RSN_CUDA(c, cudaMemsetAsync(q.flag.p, 0, (size_t)nbw * sizeof(int), c->st));
+    RSN_CUDA(c, cudaMemcpyAsync(q.col.p, memCol.data(), (size_t)S * sizeof(int), cudaMemcpyHostToDevice, c->st));
+    BlkDev hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.B = B;
+    hd.N = N;
+    hd.nchunk = nchunk;
+    hd.chunk_pts = chunk_pts;
+    hd.nchunkR = nchunkR;
+    hd.chunkR_pts = chunkR_pts;
+    RSN_CUDA(c, q.icap.ensure((size_t)nbw * sizeof(int)));
+    hd.icap = q.icap.as<int>();
+    hd.tol_in = tol_in;
+    hd.blist = q.blist.as<int>();
+    hd.col = q.col.as<int>();
+    hd.gl = c->gld.as<double>();
+    hd.xi = q.xi.as<double2>();
+    hd.QQ = q.QQ.as<double2>();
+    hd.xi0n = q.xi0n.as<double>();
+    hd.part = q.part.as<double2>();
+    hd.alpha = q.alpha.as<float2>();
+    hd.axi = q.axi.as<float2>();
+    hd.tinv = q.tinv.as<float2>();
+    hd.tinv64 = q.tinv64.as<double2>();
+    hd.beta = q.beta.as<float2>();
+    hd.flag = q.flag.as<int>();
+    hd.its = q.its.as<int>();
+    hd.W = q.W.as<float2>();
+    hd.P = q.P.as<float2>();
+    hd.AP = q.AP.as<float2>();
+    hd.D = q.D.as<float2>();
+    hd.X = q.X.as<double2>();
+    hd.R = q.R.as<double2>();
+    hd.rpart = q.rpart.as<double>();
+    hd.rn = q.rn.as<double>();
+    hd.tt = q.tt.as<double>();
+    RSN_CUDA(c, cudaMemcpyAsync(q.dev.p, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->st));
+    const BlkDev* dd = q.dev.as<BlkDev>();
+    // operator tilings: FP32 apply of P, FP64 apply of X
+    const bool al32 = (N * (long long)sizeof(float2)) % 16 == 0;
+    const Tiling t32 = choose_tiling(c, false, OP_APPLY, S, al32);
+    const Tiling t64 = choose_tiling(c, true, OP_APPLY, S, false);
+    {
+      JuncDev js[2] = {c->jh, c->jh};
+      const Tiling* tt2[2] = {&t32, &t64};
+      for (int k = 0; k < 2; ++k) {
+        const Tiling& t = *tt2[k];
+        js[k].TY = t.TY;
+        js[k].Lz = t.Lz;
+        js[k].ytiles = t.ytiles;
+        js[k].ztiles = t.ztiles;
+        js[k].nA = t.n;
+        js[k].nR = t.n;
+        js[k].kind = t.plane ? kOpPlane : t.pair ? kOpPair : t.tma ? kOpTma : kOpReg;
+      }
+      RSN_CUDA(c, cudaMemcpyAsync(q.jd.p, js, 2 * sizeof(JuncDev), cudaMemcpyHostToDevice, c->st));
+    }
+    const JuncDev* j32 = q.jd.as<JuncDev>();
+    const JuncDev* j64 = q.jd.as<JuncDev>() + 1;
+    // outer loop
+    std::vector<int> act(nbw);
+    for (int k = 0; k < nbw; ++k) act[k] = k;
+    std::vector<double> rn(S), tt(S), rn_prev(S, 1.0), t_prev(S, 0.0), dt_prev(S, HUGE_VAL);
+    std::vector<long long> apps(nbw, 0);
+    std::vector<int> stall(nbw, 0), failed(nbw, 0), flags(nbw), its(nbw);
+    // Inner iteration cap per block: the first inner solve (from the unit
+    // columns) may take up to min(max_iter, kBlkInnerCap); a restart that runs
+    // past twice the first solve's count has lost its block's orthogonality
+    // (FP32 Gram matrices of nearly dependent residual directions) and is
+    // abandoned, the block going to the plain solver.
+    std::vector<int> icap(nbw, std::min(o->max_iter, kBlkInnerCap));
+    for (int outer = 0;; ++outer) {
+      if (o->deadline_ms > 0) {
+        const double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        if (el > o->deadline_ms) {
+          for (int k : act) failed[k] = 2;
+          break;
+        }
+      }
+      if (outer > 0) {
+        // an inner solve that hit its cap or broke down leaves a correction of
+        // unknown quality: its block keeps its last FP64 iterate and goes to the
+        // plain solver
+        std::vector<int> good;
+        for (int k : act)
+          if (flags[k] == 1) good.push_back(k);
+          else failed[k] = 1;
+        act.swap(good);
+        if (act.empty()) break;
+      }
+      const int na = (int)act.size();
+      if ((rs = blk_set_lists(c, br, act, memE)) != RSN_OK) return rs;
+      if (outer > 0) {
+        RSN_CUDA(c, launch_blk_xupd(B, na, c->st, dd, N));
+        if ((rs = blk_apply(c, t64, j64, false, na * B, q.X.p, q.R.p)) != RSN_OK) return rs;
+        for (int k : act) apps[k] += 1;
+      }
+      RSN_CUDA(c, launch_blk_resid(B, na, nchunkR, outer > 0, c->st, dd));
+      RSN_CUDA(c, launch_blk_norm(B, na, nchunkR, c->st, dd));
+      c->st_launches += outer > 0 ? 3 : 2;
+      RSN_CUDA(c, cudaMemcpyAsync(rn.data(), q.rn.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      RSN_CUDA(c, cudaMemcpyAsync(tt.data(), q.tt.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      int hstat[4] = {0, 0, 0, 0};
+      RSN_CUDA(c, cudaMemcpyAsync(hstat, q.stat.p, sizeof(hstat), cudaMemcpyDeviceToHost, c->st));
+      RSN_CUDA(c, cudaStreamSynchronize(c->st));
+      if (hstat[2]) {
+        leave(c);
+        RSN_FAIL(c, RSN_ETIMEOUT, "an operator kernel gave up waiting for a bulk copy");
+      }
+      std::vector<int> keep;
+      for (int k : act) {
+        bool all = true, progress = false;
+        for (int a = 0; a < B; ++a) {
+          const int v = k * B + a;
+          if (memOut[v] < 0) continue;
+          bool ok = std::isfinite(rn[v]) && rn[v] <= o->tol;
+          if (ok && o->tol_T > 0.0) {
+            if (outer < 2) {
+              ok = false;
+            } else {
+              const double dt = std::fabs(tt[v] - t_prev[v]);
+              const double red = std::min(1.0, 10.0 * rn[v] / std::max(rn_prev[v], 1e-300));
+              ok = dt * red <= o->tol_T * tt[v] || dt == 0.0;
+            }
+          }
+          if (!ok) all = false;
+          // progress: the residual halved, or (at the residual target) the T
+          // partial's change halved
+          const double dt = std::fabs(tt[v] - t_prev[v]);
+          if (outer == 0 || rn[v] < 0.5 * rn_prev[v] || (rn[v] <= o->tol && dt < 0.5 * dt_prev[v])) progress = true;
+        }
+        for (int a = 0; a < B; ++a) {
+          const int v = k * B + a;
+          if (outer > 0) dt_prev[v] = std::fabs(tt[v] - t_prev[v]);
+          rn_prev[v] = rn[v];
+          t_prev[v] = tt[v];
+        }
+        if (all) continue;
+        stall[k] = progress ? 0 : stall[k] + 1;
+        if (stall[k] >= 3 || outer >= o->max_outer) {
+          failed[k] = 1;
+          continue;
+        }
+        keep.push_back(k);
+      }
+      act.swap(keep);
+      if (act.empty()) break;
+      // inner solve on the normalised residual block
+      const int na2 = (int)act.size();
+      if ((rs = blk_set_lists(c, br, act, memE)) != RSN_OK) return rs;
+      // the previous inner solve left its end state in the flags; the kernels
+      // of the new one (the Gram of W_0 first) run only on unflagged blocks
+      RSN_CUDA(c, cudaMemsetAsync(q.flag.p, 0, (size_t)nbw * sizeof(int), c->st));
+      RSN_CUDA(c, cudaMemcpyAsync(q.icap.p, icap.data(), (size_t)nbw * sizeof(int), cudaMemcpyHostToDevice, c->st));
+      RSN_CUDA(c, launch_blk_scale(B, na2, c->st, dd, N));
+      RSN_CUDA(c, launch_blk_gram64(B, na2, nchunk, c->st, dd));
+      RSN_CUDA(c, launch_blk_small(B, 0, na2, c->st, dd));
+      RSN_CUDA(c, launch_blk_q0(B, na2, c->st, dd, N));
+      c->st_launches += 4;
+      std::vector<int> in = act;
+      const int kChunk = 8;
+      while (!in.empty()) {
+        const int ni = (int)in.size();
+        for (int it = 0; it < kChunk; ++it) {
+          RSN_CUDA(c, launch_blk_comb_p(B, ni, c->st, dd, N));
+          if ((rs = blk_apply(c, t32, j32, true, ni * B, q.P.p, q.AP.p)) != RSN_OK) return rs;
+          RSN_CUDA(c, launch_blk_gram(B, 0, ni, nchunk, c->st, dd));
+          RSN_CUDA(c, launch_blk_small(B, 1, ni, c->st, dd));
+          RSN_CUDA(c, launch_blk_comb_w(B, ni, c->st, dd, N));
+          RSN_CUDA(c, launch_blk_gram(B, 1, ni, nchunk, c->st, dd));
+          RSN_CUDA(c, launch_blk_small(B, 2, ni, c->st, dd));
+          c->st_launches += 6;
+        }
+        RSN_CUDA(c, cudaMemcpyAsync(flags.data(), q.flag.p, (size_t)nbw * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        RSN_CUDA(c, cudaStreamSynchronize(c->st));
+        std::vector<int> nxt;
+        for (int k : in)
+          if (flags[k] == 0) nxt.push_back(k);
+        if (nxt.size() != in.size()) {
+          in.swap(nxt);
+          if (!in.empty() && (rs = blk_set_lists(c, br, in, memE)) != RSN_OK) return rs;
+        }
+      }
+      RSN_CUDA(c, cudaMemcpyAsync(its.data(), q.its.p, (size_t)nbw * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      RSN_CUDA(c, cudaStreamSynchronize(c->st));
+      for (int k : act) {
+        apps[k] += its[k];
+        if (flags[k] == 2) ++n_brk;
+        if (outer == 0) icap[k] = std::min(icap[k], std::max(64, 2 * its[k]));
+      }
+    }
+    // Blocks that did not finish: their columns go to the plain slot-pool
+    // solver (FP32 recurrence with FP64 reliable updates and its own FP64
+    // re-solve of stalled systems), warm-started from the block's last FP64
+    // iterate.
+    std::vector<int> hv;
+    for (int k = 0; k < nbw; ++k)
+      if (failed[k] == 1)
+        for (int a = 0; a < B; ++a)
+          if (memOut[k * B + a] >= 0) hv.push_back(k * B + a);
+    std::vector<int> hst(S, 0), hit(S, 0);
+    if (!hv.empty()) {
+      const int nh = (int)hv.size();
+      StreamIn in;
+      in.resize(nh);
+      for (int u = 0; u < nh; ++u) {
+        in.E[u] = memE[hv[u]];
+        in.col[u] = memCol[hv[u]];
+        in.xo[u] = (long long)hv[u] * N;
+        in.bn2[u] = 1.0;  // ||e_col||^2: start from the iterate in X
+      }
+      StreamOut so;
+      if ((rs = run_stream(c, o, in, q.X.as<double2>(), nullptr, true, 0, t_start, so)) != RSN_OK) return rs;
+      std::vector<double> th(nh);
+      RSN_CUDA(c, cudaMemcpyAsync(th.data(), c->cb.out_t.p, nh * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      RSN_CUDA(c, cudaStreamSynchronize(c->st));
+      std::vector<int> F;
+      StreamIn sub;
+      for (int u = 0; u < nh; ++u) {
+        const int v = hv[u];
+        tt[v] = th[u];
+        rn[v] = so.relres[u];
+        hit[v] = so.iters[u];
+        hst[v] = so.status[u];
+        if (so.status[u] != 0 && o->precision == RSN_MIXED) {
+          F.push_back(u);
+          sub.push(in, (size_t)u);
+          sub.bn2.back() = 0.0;  // cold start: a stalled FP32 iterate slows FP64 COCG down
+        }
+      }
+      if (!F.empty()) {
+        rsn_solver_opts o64;
+        rsn_default_opts(RSN_FP64, &o64);
+        o64.tol = o->tol;
+        o64.tol_T = o->tol_T;
+        o64.deadline_ms = o->deadline_ms;
+        StreamOut s2;
+        if ((rs = run_stream(c, &o64, sub, q.X.as<double2>(), nullptr, true, 0, t_start, s2)) != RSN_OK) return rs;
+        std::vector<double> t2(F.size());
+        RSN_CUDA(c, cudaMemcpyAsync(t2.data(), c->cb.out_t.p, F.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->st));
+        RSN_CUDA(c, cudaStreamSynchronize(c->st));
+        for (size_t f = 0; f < F.size(); ++f) {
+          const int v = hv[F[f]];
+          tt[v] = t2[f];
+          rn[v] = s2.relres[f];
+          hit[v] += s2.iters[f];
+          hst[v] = s2.status[f];
+        }
+      }
+      n_hand += nh;
+    }
+    // outputs of the real members
+    for (int k = 0; k < nbw; ++k) {
+      if (failed[k] == 2) ++n_late;
+      for (int a = 0; a < B; ++a) {
+        const int v = k * B + a;
+        const long long out = memOut[v];
+        if (out < 0) continue;
+        t_host[out] = tt[v];
+        if (t_out) t_out[out] = tt[v];
+        const bool bad = failed[k] == 2 || (failed[k] == 1 && hst[v] != 0);
+        if (bad && failed[k] == 1) ++n_fail;
+        if (iters) iters[out] = bad ? -1 : (int32_t)std::min<long long>(apps[k] + hit[v], INT32_MAX);
+        if (relres) relres[out] = rn[v];
+        c->st_iters += apps[k];
+        if (x_out)
+          RSN_CUDA(c, cudaMemcpyAsync(x_out + out * N, q.X.as<double2>() + (size_t)v * N, N * sizeof(double2),
+                                      cudaMemcpyDeviceToDevice, c->st));
+      }
+    }
+  }
+  if (n_fail > 0) worst = RSN_ENOCONV;
+  if (n_late > 0) worst = RSN_ETIMEOUT;
+  if (T && n_e > 0) {
+    RSN_CUDA(c, q.t_all.ensure(t_host.size() * sizeof(double)));
+    RSN_CUDA(c, q.gr_cols.ensure(std::max(1, n_cols) * sizeof(double)));
+    RSN_CUDA(c, q.Td.ensure(n_e * sizeof(double)));
+    std::vector<double> hgr(std::max(1, n_cols));
+    for (int k = 0; k < n_cols; ++k) hgr[k] = c->gr[cols[k]];
+    RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, t_host.data(), t_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    RSN_CUDA(c, cudaMemcpyAsync(q.gr_cols.p, hgr.data(), hgr.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    if (n_cols > 0) {
+      RSN_CUDA(c, launch_t_final(n_e, n_cols, c->st, q.t_all.as<double>(), q.gr_cols.as<double>(), q.Td.as<double>()));
+      c->st_launches += 1;
+    } else {
+      RSN_CUDA(c, cudaMemsetAsync(q.Td.p, 0, n_e * sizeof(double), c->st));
+    }
+    RSN_CUDA(c, cudaMemcpyAsync(T, q.Td.p, n_e * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  }
+  RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
+  RSN_CUDA(c, cudaStreamSynchronize(c->st));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->t0, c->t1);
+  c->st_ms = ms;
+  c->st_fallback = n_hand;
+  (void)n_brk;
+  if ((rs = leave(c)) != RSN_OK) return rs;
+  if (worst != RSN_OK)
+    RSN_FAIL(c, worst, "%lld columns did not reach tol / tol_T, %lld blocks stopped at the deadline", n_fail, n_late);
+  return RSN_OK;
+}
+
+extern "C" {
+
+rsn_status rsn_solve_columns_block(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols, int block,
+                                   double tol_inner, const rsn_solver_opts* o, void* x_dev, double* t_cols,
+                                   int32_t* iters, double* relres) {
+  if (!c) return RSN_EINVAL;
+  if ((long long)n_e * n_cols > 0 && !x_dev) RSN_FAIL(c, RSN_EINVAL, "x_dev is NULL");
+  return block_impl(c, n_e, E, n_cols, cols, block, tol_inner, o, reinterpret_cast<double2*>(x_dev), t_cols, nullptr,
+                    iters, relres);
+}
+
+rsn_status rsn_transmission_block(rsn_ctx* c, int n_e, const double* E, int n_cols, const int32_t* cols, int block,
+                                  double tol_inner, const rsn_solver_opts* o, double* T, double* t_cols,
+                                  int32_t* iters) {
+  if (!c) return RSN_EINVAL;
+  if (n_e > 0 && !T) RSN_FAIL(c, RSN_EINVAL, "T is NULL");
+  return block_impl(c, n_e, E, n_cols, cols, block, tol_inner, o, nullptr, t_cols, T, iters, nullptr);
 }
 
 }  // extern "C"

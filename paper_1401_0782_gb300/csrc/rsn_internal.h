@@ -23,8 +23,8 @@ constexpr int kMaxGroupNp = 16; // projectors per atom (s,p,d = 9)
 // by the zero-padded tail of an atom's last value quad
 constexpr int kCePad = 16;
 constexpr int kMaxGraphIters = 256;
-constexpr int kMaxApplyRhs = 65535;
-constexpr int kMaxGoalChecks = 24;   // T checks of a goal phase before it ends  // vectors per operator-application call (grid y dimension)
+constexpr int kMaxApplyRhs = 65535;  // vectors per operator-application call (grid y dimension)
+constexpr int kMaxGoalChecks = 24;   // T checks of a goal phase before it ends
 constexpr int kSchedThreads = 1024;
 // CTA rows of the kernels that work only on NEW / CHECK slots (zero, true
 // residual and its projections, x update): each row takes list entries
@@ -155,9 +155,11 @@ struct BatchDev {
   double* out_t;             // T partial sum_{i in L} Gamma_L |x(i)|^2 per system (may be null)
   int* sched;                // [0] next system, [1] busy slots, [3 + it] busy after iteration it of a
                              // replay, [3 + kMaxGraphIters + it] systems that did a COCG iteration
+                             // (zeroed at the start of each replay)
   unsigned long long* counters;  // [0] COCG iterations, [1] reliable updates, [2] finished, [3] not converged
   int* lst;                  // NEW / CHECK slots of the current iteration, in slot order
   int* lst_n;                // their number
+  int* inlist;               // [S] 1: the slot is in this iteration's list
   int* fslot;                // FREE slots in slot order (scheduler scratch)
   void* c_e;                 // e_kb[p] c_p[p] of the current direction per slot (inner precision),
   int ce_stride;             // n_proj + kCePad entries per slot, the last kCePad always zero
@@ -190,6 +192,68 @@ struct BatchDev {
   int stall_cap;  // true residuals in a row without a 4x gain before a system is handed back (0 = never)
   int handback;   // 1: systems whose predicted iteration count exceeds max_iter are handed back early
 };
+
+// Block COCG: the B columns of one energy share one block Krylov space
+// (A(E) = A(E)^T, so the COCG recurrence carries over to blocks with the
+// unconjugated bilinear form).  The residual block is kept orthonormal,
+// R_k = Q_k xi_k with Q_k = W_k tau_k^{-1} (Cholesky QR of W_k), so columns
+// that converge at different rates do not make the b x b systems singular.
+// The block recurrence runs in complex FP32; the b x b algebra in FP64; an FP64
+// true residual restarts it (defect correction) until every column meets its
+// residual and T-partial targets.
+constexpr int kBlkThreads = 256;  // vector kernels and the Gram kernel
+constexpr int kBlkTile = 64;      // points per shared-memory tile of the Gram kernel
+constexpr int kBlkMax = 16;       // largest block
+constexpr int kBlkInnerCap = 1000; // iterations of one inner solve before it is abandoned
+
+struct BlkDev {
+  int B;                  // columns per block (4, 8 or 16)
+  long long N;
+  int nchunk;             // Gram partial sums per block
+  long long chunk_pts;    // points per Gram chunk (a multiple of kBlkTile)
+  int nchunkR;            // residual partial sums per vector
+  long long chunkR_pts;
+  const int* icap;        // [nb] inner iterations before an inner solve of the block ends unconverged
+  double tol_in;          // inner solve: each column's residual reduced by this factor
+  const int* blist;       // blocks of this launch (grid.y), host-compacted
+  const int* col;         // [nb*B] right-hand side e_col of each member
+  const double* gl;       // Gamma_L
+  // b x b state per block, row-major [row * B + col]
+  double2* xi;            // R_k = Q_k xi_k
+  double2* QQ;            // Q_k^T Q_k
+  double* xi0n;           // [nb][B] column norms of xi_0
+  double2* part;          // [nb][nchunk][2][B*B] Gram partials
+  float2* alpha;          // alpha_k = (P^T A P)^{-1} Q^T Q
+  float2* axi;            // alpha_k xi_k
+  float2* tinv;           // tau_k^{-1} (upper triangular)
+  double2* tinv64;        // tau_0^{-1} of a restart (FP64)
+  float2* beta;           // beta_k = (Q_k^T Q_k)^{-1} tau_{k+1}^T Q_{k+1}^T Q_{k+1}
+  int* flag;              // [nb] 0 iterating, 1 converged, 2 breakdown, 3 iteration cap
+  int* its;               // [nb] iterations of the current inner solve
+  // vectors: member a of block k at ((k * B + a) * N)
+  float2* W;
+  float2* P;
+  float2* AP;
+  float2* D;              // inner solution (correction of the normalised residual block)
+  double2* X;             // FP64 iterate
+  double2* R;             // FP64 residual b - A X (the FP64 operator writes A X here first),
+                          // normalised per member at a restart
+  double* rpart;          // [nb*B][nchunkR][2] partials of ||r||^2 and sum Gamma_L |x|^2
+  double* rn;             // [nb*B] ||r|| of the current outer step
+  double* tt;             // [nb*B] sum_{i in L} Gamma_L |x(i)|^2
+};
+
+cudaError_t launch_blk_comb_p(int B, int nb, cudaStream_t st, const BlkDev* d, long long N);
+cudaError_t launch_blk_comb_w(int B, int nb, cudaStream_t st, const BlkDev* d, long long N);
+cudaError_t launch_blk_gram(int B, int mode, int nb, int nchunk, cudaStream_t st, const BlkDev* d);
+cudaError_t launch_blk_small(int B, int phase, int nb, cudaStream_t st, const BlkDev* d);
+cudaError_t launch_blk_gram64(int B, int nb, int nchunk, cudaStream_t st, const BlkDev* d);
+cudaError_t launch_blk_q0(int B, int nb, cudaStream_t st, const BlkDev* d, long long N);
+// outer step kernels over the members of the listed blocks
+cudaError_t launch_blk_resid(int B, int nb, int nchunkR, bool have_ax, cudaStream_t st, const BlkDev* d);
+cudaError_t launch_blk_norm(int B, int nb, int nchunkR, cudaStream_t st, const BlkDev* d);
+cudaError_t launch_blk_scale(int B, int nb, cudaStream_t st, const BlkDev* d, long long N);
+cudaError_t launch_blk_xupd(int B, int nb, cudaStream_t st, const BlkDev* d, long long N);
 
 enum OpMode { OP_COCG = 0, OP_RESID = 1, OP_APPLY = 2 };
 // operator kernels; a slot pool over several junctions launches each kind its

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kSchedThreads) list_kernel(const BatchDev* __r
     int st = SL_FREE;
     if (s < b.nslots) st = b.state[s];
     const bool in = st == SL_NEW || st == SL_CHECK || st == SL_CHECKT;
+    if (s < b.nslots) b.inlist[s] = in ? 1 : 0;
     const unsigned m = __ballot_sync(0xffffffffu, in);
     if (lane == 0) warp_cnt[warp] = __popc(m);
     __syncthreads();
@@ -377,7 +378,8 @@ __global__ void __launch_bounds__(32 * kBookWarps) book_kernel(const JuncDev* __
 }
 
 // ---------------------------------------------------------------------------
-// Scheduler (one CTA, after the true-residual kernel): finishes converged
+// Scheduler (one CTA, after the true-residual path and the COCG step of the
+// same iteration): finishes converged
 // systems, performs reliable updates (the true FP64 residual replaces the
 // recurrence residual, the search direction is kept), frees drained slots and
 // assigns queued systems to free slots in slot order.
@@ -391,9 +393,13 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
   int upd = 0, busy = 0;
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
     int st = b.state[s];
+    // NEW / CHECK / CHECKT slots are handled only if this iteration's list took
+    // them (their true residual or goal check ran): the bookkeeping kernel, which
+    // runs beside the list path, can move a slot to CHECK after the list was made
+    const bool listed = b.inlist[s] != 0;
     if (st == SL_DRAIN) {
       st = SL_FREE;
-    } else if (st == SL_CHECKT) {
+    } else if (st == SL_CHECKT && listed) {
       // goal phase: compare the T partial of the iterate with the previous check;
       // the recurrence continues untouched towards a tenfold lower residual
       const double tcur = b.tgoal[s], tl = b.tlast[s];
@@ -418,7 +424,7 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
         b.cyc_iters[s] = 0;
         st = SL_ACTIVE;
       }
-    } else if (st == SL_NEW || st == SL_CHECK) {
+    } else if ((st == SL_NEW || st == SL_CHECK) && listed) {
       const JuncDev& J = jt[b.junc[s]];
       double nrm = 0.0, tcur = 0.0;
       double2 rho = make_double2(0.0, 0.0);
@@ -623,7 +629,6 @@ __global__ void __launch_bounds__(kSchedThreads) sched_kernel(const JuncDev* __r
     b.sched[0] = s_first;
     b.sched[1] = (int)out[0];
     b.sched[3 + slot_it] = (int)out[0];
-    b.sched[3 + kMaxGraphIters + slot_it] = 0;  // counted by the bookkeeping kernel of this iteration
     b.counters[1] += (unsigned long long)out[1];
   }
 }
