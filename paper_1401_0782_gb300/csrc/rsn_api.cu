@@ -1731,6 +1731,8 @@ static rsn_status block_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, c
       if (sc[k] == sc[k - 1]) RSN_FAIL(c, RSN_EINVAL, "column %d appears twice (a block needs distinct columns)", sc[k]);
   }
   if ((rs = enter(c)) != RSN_OK) return rs;
+  // every exit after enter() orders the caller's stream after the queued work
+  auto run = [&]() -> rsn_status {
   reset_stats(c);
   BlkBufs& q = c->bb;
   const auto t_start = std::chrono::steady_clock::now();
@@ -1742,10 +1744,8 @@ static rsn_status block_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, c
     std::sort(sc.begin(), sc.end());
     for (long long i = 0; i < N && (int)pad.size() < B; ++i)
       if (!std::binary_search(sc.begin(), sc.end(), (int32_t)i)) pad.push_back((int)i);
-    if ((int)pad.size() < (B - n_cols % B) % B) {
-      leave(c);
+    if ((int)pad.size() < (B - n_cols % B) % B)
       RSN_FAIL(c, RSN_EINVAL, "too few grid points outside the column set to pad the last block");
-    }
   }
   const int nbe = (n_cols + B - 1) / B;  // blocks per energy
   const long long nb = (long long)n_e * nbe;
@@ -1933,10 +1933,7 @@ static rsn_status block_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, c
       int hstat[4] = {0, 0, 0, 0};
       RSN_CUDA(c, cudaMemcpyAsync(hstat, q.stat.p, sizeof(hstat), cudaMemcpyDeviceToHost, c->st));
       RSN_CUDA(c, cudaStreamSynchronize(c->st));
-      if (hstat[2]) {
-        leave(c);
-        RSN_FAIL(c, RSN_ETIMEOUT, "an operator kernel gave up waiting for a bulk copy");
-      }
+      if (hstat[2]) RSN_FAIL(c, RSN_ETIMEOUT, "an operator kernel gave up waiting for a bulk copy");
       std::vector<int> keep;
       for (int k : act) {
         bool all = true, progress = false;
@@ -2125,10 +2122,13 @@ static rsn_status block_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, c
   c->st_ms = ms;
   c->st_fallback = n_hand;
   (void)n_brk;
-  if ((rs = leave(c)) != RSN_OK) return rs;
   if (worst != RSN_OK)
     RSN_FAIL(c, worst, "%lld columns did not reach tol / tol_T, %lld blocks stopped at the deadline", n_fail, n_late);
   return RSN_OK;
+  };
+  rs = run();
+  const rsn_status rl = leave(c);
+  return rs != RSN_OK ? rs : rl;
 }
 
 extern "C" {
