@@ -45,16 +45,23 @@ __device__ __forceinline__ float2 cjfma_f(float2 a, float2 b, float2 acc) {
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 __device__ __forceinline__ float2 to32(double2 a) { return make_float2((float)a.x, (float)a.y); }
 
-// Kahan-compensated FP32 accumulation of complex tile sums
-__device__ __forceinline__ void kahan2(float2& s, float2& c, float2 v) {
-  float y = v.x - c.x, t = s.x + y;
-  c.x = (t - s.x) - y;
-  s.x = t;
-  y = v.y - c.y;
-  t = s.y + y;
-  c.y = (t - s.y) - y;
-  s.y = t;
+// Sums of FP32 products to about FP64 accuracy in FP32 arithmetic: each
+// product a b is split exactly into p = fl(a b) and its rounding error
+// e = fma(a, b, -p) (error-free transformation); the p are summed with Kahan's
+// compensation, the e plainly (they are ~1e-7 of the p).  The explicit _rn
+// intrinsics keep the compiler from contracting p into a later addition.
+struct KSum {
+  float s, c, e;
+};
+__device__ __forceinline__ void ks_add(KSum& k, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  k.e = __fadd_rn(k.e, __fmaf_rn(a, b, -p));
+  const float y = __fsub_rn(p, k.c);
+  const float t = __fadd_rn(k.s, y);
+  k.c = __fsub_rn(__fsub_rn(t, k.s), y);
+  k.s = t;
 }
+__device__ __forceinline__ double ks_val(const KSum& k) { return (double)k.s - (double)k.c + (double)k.e; }
 
 }  // namespace
 
@@ -157,8 +164,11 @@ __global__ void __launch_bounds__(kBlkThreads) blk_comb_w_kernel(const BlkDev* _
 // out[1] = W^T W.  Tiles of kBlkTile points of every member are staged in
 // shared memory (row pitch kBlkTile + 1 keeps the members' rows on distinct
 // banks); each thread owns a 2 x 2 tile of (a, c) pairs and a slice of the
-// tile's points; FP32 products, tile sums Kahan-accumulated in FP32, the
-// point slices and chunks summed in FP64.
+// tile's points.  The sums reach about FP64 accuracy in FP32 arithmetic
+// (error-free products, compensated sums; the point slices and chunks in
+// FP64): the block recurrence's b x b systems come from Gram matrices of
+// nearly dependent directions once its residual columns share the slowest
+// modes of A(E), and FP32 sums of them stall its restarts.
 // ---------------------------------------------------------------------------
 template <int B, int MODE>
 __global__ void __launch_bounds__(kBlkThreads) blk_gram_kernel(const BlkDev* __restrict__ dp) {
@@ -185,11 +195,14 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_kernel(const BlkDev* __r
   const int tid = threadIdx.x;
   const int t = tid % NT, g = tid / NT;
   const int a0 = 2 * (t / H), c0 = 2 * (t % H);
-  float2 s[NO][4], cmp[NO][4];
+  // [output][pair][re, im]
+  KSum ks[NO][4][2];
 #pragma unroll
   for (int o = 0; o < NO; ++o)
 #pragma unroll
-    for (int m = 0; m < 4; ++m) s[o][m] = cmp[o][m] = make_float2(0.f, 0.f);
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) ks[o][m][r] = KSum{0.f, 0.f, 0.f};
   for (long long ts = x0; ts < x1; ts += TP) {
     for (int e = tid; e < B * TP; e += kBlkThreads) {
       const int a = e / TP, ii = e % TP;
@@ -200,43 +213,39 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_kernel(const BlkDev* __r
     }
     __syncthreads();
     const float2* sv = MODE == 0 ? sV : sU;
-    float2 acc[NO][4];
-#pragma unroll
-    for (int o = 0; o < NO; ++o)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) acc[o][m] = make_float2(0.f, 0.f);
-#pragma unroll 4
+#pragma unroll 2
     for (int ii = g; ii < TP; ii += PG) {
-      const float2 u0 = sU[a0 * LD + ii], u1 = sU[(a0 + 1) * LD + ii];
-      const float2 v0 = sv[c0 * LD + ii], v1 = sv[(c0 + 1) * LD + ii];
-      if constexpr (MODE == 0) {
-        acc[0][0] = cfma_f(u0, v0, acc[0][0]);
-        acc[0][1] = cfma_f(u0, v1, acc[0][1]);
-        acc[0][2] = cfma_f(u1, v0, acc[0][2]);
-        acc[0][3] = cfma_f(u1, v1, acc[0][3]);
-      } else {
-        acc[0][0] = cjfma_f(u0, v0, acc[0][0]);
-        acc[0][1] = cjfma_f(u0, v1, acc[0][1]);
-        acc[0][2] = cjfma_f(u1, v0, acc[0][2]);
-        acc[0][3] = cjfma_f(u1, v1, acc[0][3]);
-        acc[1][0] = cfma_f(u0, v0, acc[1][0]);
-        acc[1][1] = cfma_f(u0, v1, acc[1][1]);
-        acc[1][2] = cfma_f(u1, v0, acc[1][2]);
-        acc[1][3] = cfma_f(u1, v1, acc[1][3]);
+      const float2 uu[2] = {sU[a0 * LD + ii], sU[(a0 + 1) * LD + ii]};
+      const float2 vv[2] = {sv[c0 * LD + ii], sv[(c0 + 1) * LD + ii]};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float2 u = uu[m >> 1], v = vv[m & 1];
+        if constexpr (MODE == 0) {
+          // u v
+          ks_add(ks[0][m][0], u.x, v.x);
+          ks_add(ks[0][m][0], -u.y, v.y);
+          ks_add(ks[0][m][1], u.x, v.y);
+          ks_add(ks[0][m][1], u.y, v.x);
+        } else {
+          // conj(u) v and u v
+          ks_add(ks[0][m][0], u.x, v.x);
+          ks_add(ks[0][m][0], u.y, v.y);
+          ks_add(ks[0][m][1], u.x, v.y);
+          ks_add(ks[0][m][1], -u.y, v.x);
+          ks_add(ks[1][m][0], u.x, v.x);
+          ks_add(ks[1][m][0], -u.y, v.y);
+          ks_add(ks[1][m][1], u.x, v.y);
+          ks_add(ks[1][m][1], u.y, v.x);
+        }
       }
     }
-#pragma unroll
-    for (int o = 0; o < NO; ++o)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) kahan2(s[o][m], cmp[o][m], acc[o][m]);
     __syncthreads();
   }
 #pragma unroll
   for (int o = 0; o < NO; ++o)
 #pragma unroll
     for (int m = 0; m < 4; ++m)
-      red[((o * PG + g) * NT + t) * 4 + m] =
-          make_double2((double)s[o][m].x - (double)cmp[o][m].x, (double)s[o][m].y - (double)cmp[o][m].y);
+      red[((o * PG + g) * NT + t) * 4 + m] = make_double2(ks_val(ks[o][m][0]), ks_val(ks[o][m][1]));
   __syncthreads();
   // slices summed in a fixed order; entry (a, c) of output o
   double2* out = d.part + ((size_t)k * d.nchunk + chunk) * 2 * B * B;
