@@ -1733,398 +1733,398 @@ static rsn_status block_impl(rsn_ctx* c, int n_e, const double* E, int n_cols, c
   if ((rs = enter(c)) != RSN_OK) return rs;
   // every exit after enter() orders the caller's stream after the queued work
   auto run = [&]() -> rsn_status {
-  reset_stats(c);
-  BlkBufs& q = c->bb;
-  const auto t_start = std::chrono::steady_clock::now();
-  RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
-  // padding members of a short last block: grid points outside the column set
-  std::vector<int> pad;
-  {
-    std::vector<int32_t> sc(cols, cols + n_cols);
-    std::sort(sc.begin(), sc.end());
-    for (long long i = 0; i < N && (int)pad.size() < B; ++i)
-      if (!std::binary_search(sc.begin(), sc.end(), (int32_t)i)) pad.push_back((int)i);
-    if ((int)pad.size() < (B - n_cols % B) % B)
-      RSN_FAIL(c, RSN_EINVAL, "too few grid points outside the column set to pad the last block");
-  }
-  const int nbe = (n_cols + B - 1) / B;  // blocks per energy
-  const long long nb = (long long)n_e * nbe;
-  std::vector<double> t_host((size_t)std::max(1, n_e) * std::max(1, n_cols), 0.0);
-  rsn_status worst = RSN_OK;
-  long long n_fail = 0, n_brk = 0, n_late = 0, n_hand = 0;
-  const size_t per_member = (size_t)N * (4 * sizeof(float2) + 2 * sizeof(double2)) + 4096;
-  size_t fr = 0, tot = 0;
-  cudaMemGetInfo(&fr, &tot);
-  // members per wave: within memory and within a launch's grid.y (one CTA row per member)
-  const long long cap = std::max<long long>(
-      1, std::min<long long>(kMaxApplyRhs / B, (long long)(0.5 * (double)fr / ((double)per_member * B))));
-  for (long long b0 = 0; b0 < nb; b0 += cap) {
-    BlkRun br;
-    br.B = B;
-    br.nbw = (int)std::min<long long>(cap, nb - b0);
-    br.S = br.nbw * B;
-    const int nbw = br.nbw, S = br.S;
-    // members: E, column, real (output index) or padding (-1)
-    std::vector<double> memE(S);
-    std::vector<int> memCol(S);
-    std::vector<long long> memOut(S);
-    for (int k = 0; k < nbw; ++k) {
-      const long long gb = b0 + k;
-      const int e = (int)(gb / nbe), cb = (int)(gb % nbe);
-      int np = 0;
-      for (int a = 0; a < B; ++a) {
-        const int kc = cb * B + a;
-        const int v = k * B + a;
-        memE[v] = E[e];
-        if (kc < n_cols) {
-          memCol[v] = cols[kc];
-          memOut[v] = (long long)e * n_cols + kc;
-        } else {
-          memCol[v] = pad[np++];
-          memOut[v] = -1;
-        }
-      }
-    }
-    // buffers
-    const size_t vb32 = (size_t)S * N * sizeof(float2), vb64 = (size_t)S * N * sizeof(double2);
-    RSN_CUDA(c, q.W.ensure(vb32));
-    RSN_CUDA(c, q.P.ensure(vb32));
-    RSN_CUDA(c, q.AP.ensure(vb32));
-    RSN_CUDA(c, q.D.ensure(vb32));
-    RSN_CUDA(c, q.X.ensure(vb64));
-    RSN_CUDA(c, q.R.ensure(vb64));
-    int nchunk = std::max(1, std::min(64, (4 * 152 + nbw - 1) / nbw));
-    long long chunk_pts = (N + nchunk - 1) / nchunk;
-    chunk_pts = (chunk_pts + kBlkTile - 1) / kBlkTile * kBlkTile;
-    nchunk = (int)((N + chunk_pts - 1) / chunk_pts);
-    int nchunkR = std::max(1, std::min(32, (8 * 152 + S - 1) / S));
-    long long chunkR_pts = (N + nchunkR - 1) / nchunkR;
-    nchunkR = (int)((N + chunkR_pts - 1) / chunkR_pts);
-    const size_t bb2 = (size_t)nbw * B * B;
-    RSN_CUDA(c, q.part.ensure((size_t)nbw * nchunk * 2 * B * B * sizeof(double2)));
-    RSN_CUDA(c, q.xi.ensure(bb2 * sizeof(double2)));
-    RSN_CUDA(c, q.QQ.ensure(bb2 * sizeof(double2)));
-    RSN_CUDA(c, q.xi0n.ensure((size_t)S * sizeof(double)));
-    RSN_CUDA(c, q.alpha.ensure(bb2 * sizeof(float2)));
-    RSN_CUDA(c, q.axi.ensure(bb2 * sizeof(float2)));
-    RSN_CUDA(c, q.tinv.ensure(bb2 * sizeof(float2)));
-    RSN_CUDA(c, q.tinv64.ensure(bb2 * sizeof(double2)));
-    RSN_CUDA(c, q.beta.ensure(bb2 * sizeof(float2)));
-    RSN_CUDA(c, q.flag.ensure((size_t)nbw * sizeof(int)));
-    RSN_CUDA(c, q.its.ensure((size_t)nbw * sizeof(int)));
-    RSN_CUDA(c, q.rpart.ensure((size_t)S * nchunkR * 2 * sizeof(double)));
-    RSN_CUDA(c, q.rn.ensure((size_t)S * sizeof(double)));
-    RSN_CUDA(c, q.tt.ensure((size_t)S * sizeof(double)));
-    RSN_CUDA(c, q.blist.ensure((size_t)nbw * sizeof(int)));
-    RSN_CUDA(c, q.col.ensure((size_t)S * sizeof(int)));
-    RSN_CUDA(c, q.vE.ensure((size_t)S * sizeof(double)));
-    RSN_CUDA(c, q.vjunc.ensure((size_t)S * sizeof(int)));
-    RSN_CUDA(c, q.voff.ensure((size_t)S * sizeof(long long)));
-    RSN_CUDA(c, q.cbuf.ensure((size_t)S * std::max(1, c->n_proj) * sizeof(double2)));
-    RSN_CUDA(c, q.dev.ensure(sizeof(BlkDev)));
-    RSN_CUDA(c, q.bdev.ensure(sizeof(BatchDev)));
-    RSN_CUDA(c, q.jd.ensure(2 * sizeof(JuncDev)));
-    RSN_CUDA(c, q.stat.ensure(4 * sizeof(int)));
-    RSN_CUDA(c, cudaMemsetAsync(q.stat.p, 0, 4 * sizeof(int), c->st));
-    RSN_CUDA(c, cudaMemsetAsync(q.vjunc.p, 0, (size_t)S * sizeof(int), c->st));
-    RSN_CUDA(c, cudaMemsetAsync(q.X.p, 0, vb64, c->st));
-    RSN_CUDA(c, cudaMemsetAsync(q.flag.p, 0, (size_t)nbw * sizeof(int), c->st));
-    RSN_CUDA(c, cudaMemcpyAsync(q.col.p, memCol.data(), (size_t)S * sizeof(int), cudaMemcpyHostToDevice, c->st));
-    BlkDev hd;
-    memset(&hd, 0, sizeof(hd));
-    hd.B = B;
-    hd.N = N;
-    hd.nchunk = nchunk;
-    hd.chunk_pts = chunk_pts;
-    hd.nchunkR = nchunkR;
-    hd.chunkR_pts = chunkR_pts;
-    RSN_CUDA(c, q.icap.ensure((size_t)nbw * sizeof(int)));
-    hd.icap = q.icap.as<int>();
-    hd.tol_in = tol_in;
-    hd.blist = q.blist.as<int>();
-    hd.col = q.col.as<int>();
-    hd.gl = c->gld.as<double>();
-    hd.xi = q.xi.as<double2>();
-    hd.QQ = q.QQ.as<double2>();
-    hd.xi0n = q.xi0n.as<double>();
-    hd.part = q.part.as<double2>();
-    hd.alpha = q.alpha.as<float2>();
-    hd.axi = q.axi.as<float2>();
-    hd.tinv = q.tinv.as<float2>();
-    hd.tinv64 = q.tinv64.as<double2>();
-    hd.beta = q.beta.as<float2>();
-    hd.flag = q.flag.as<int>();
-    hd.its = q.its.as<int>();
-    hd.W = q.W.as<float2>();
-    hd.P = q.P.as<float2>();
-    hd.AP = q.AP.as<float2>();
-    hd.D = q.D.as<float2>();
-    hd.X = q.X.as<double2>();
-    hd.R = q.R.as<double2>();
-    hd.rpart = q.rpart.as<double>();
-    hd.rn = q.rn.as<double>();
-    hd.tt = q.tt.as<double>();
-    RSN_CUDA(c, cudaMemcpyAsync(q.dev.p, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->st));
-    const BlkDev* dd = q.dev.as<BlkDev>();
-    // operator tilings: FP32 apply of P, FP64 apply of X
-    const bool al32 = (N * (long long)sizeof(float2)) % 16 == 0;
-    const Tiling t32 = choose_tiling(c, false, OP_APPLY, S, al32);
-    const Tiling t64 = choose_tiling(c, true, OP_APPLY, S, false);
+    reset_stats(c);
+    BlkBufs& q = c->bb;
+    const auto t_start = std::chrono::steady_clock::now();
+    RSN_CUDA(c, cudaEventRecord(c->t0, c->st));
+    // padding members of a short last block: grid points outside the column set
+    std::vector<int> pad;
     {
-      JuncDev js[2] = {c->jh, c->jh};
-      const Tiling* tt2[2] = {&t32, &t64};
-      for (int k = 0; k < 2; ++k) {
-        const Tiling& t = *tt2[k];
-        js[k].TY = t.TY;
-        js[k].Lz = t.Lz;
-        js[k].ytiles = t.ytiles;
-        js[k].ztiles = t.ztiles;
-        js[k].nA = t.n;
-        js[k].nR = t.n;
-        js[k].kind = t.plane ? kOpPlane : t.pair ? kOpPair : t.tma ? kOpTma : kOpReg;
-      }
-      RSN_CUDA(c, cudaMemcpyAsync(q.jd.p, js, 2 * sizeof(JuncDev), cudaMemcpyHostToDevice, c->st));
+      std::vector<int32_t> sc(cols, cols + n_cols);
+      std::sort(sc.begin(), sc.end());
+      for (long long i = 0; i < N && (int)pad.size() < B; ++i)
+        if (!std::binary_search(sc.begin(), sc.end(), (int32_t)i)) pad.push_back((int)i);
+      if ((int)pad.size() < (B - n_cols % B) % B)
+        RSN_FAIL(c, RSN_EINVAL, "too few grid points outside the column set to pad the last block");
     }
-    const JuncDev* j32 = q.jd.as<JuncDev>();
-    const JuncDev* j64 = q.jd.as<JuncDev>() + 1;
-    // outer loop
-    std::vector<int> act(nbw);
-    for (int k = 0; k < nbw; ++k) act[k] = k;
-    std::vector<double> rn(S), tt(S), rn_prev(S, 1.0), t_prev(S, 0.0), dt_prev(S, HUGE_VAL);
-    std::vector<long long> apps(nbw, 0);
-    std::vector<int> stall(nbw, 0), failed(nbw, 0), flags(nbw), its(nbw);
-    // Inner iteration cap per block: the first inner solve (from the unit
-    // columns) may take up to min(max_iter, kBlkInnerCap); a restart that runs
-    // past twice the first solve's count has lost its block's orthogonality
-    // (FP32 Gram matrices of nearly dependent residual directions) and is
-    // abandoned, the block going to the plain solver.
-    std::vector<int> icap(nbw, std::min(o->max_iter, kBlkInnerCap));
-    for (int outer = 0;; ++outer) {
-      if (o->deadline_ms > 0) {
-        const double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-        if (el > o->deadline_ms) {
-          for (int k : act) failed[k] = 2;
-          break;
-        }
-      }
-      if (outer > 0) {
-        // an inner solve that hit its cap or broke down leaves a correction of
-        // unknown quality: its block keeps its last FP64 iterate and goes to the
-        // plain solver
-        std::vector<int> good;
-        for (int k : act)
-          if (flags[k] == 1) good.push_back(k);
-          else failed[k] = 1;
-        act.swap(good);
-        if (act.empty()) break;
-      }
-      const int na = (int)act.size();
-      if ((rs = blk_set_lists(c, br, act, memE)) != RSN_OK) return rs;
-      if (outer > 0) {
-        RSN_CUDA(c, launch_blk_xupd(B, na, c->st, dd, N));
-        if ((rs = blk_apply(c, t64, j64, false, na * B, q.X.p, q.R.p)) != RSN_OK) return rs;
-        for (int k : act) apps[k] += 1;
-      }
-      RSN_CUDA(c, launch_blk_resid(B, na, nchunkR, outer > 0, c->st, dd));
-      RSN_CUDA(c, launch_blk_norm(B, na, nchunkR, c->st, dd));
-      c->st_launches += outer > 0 ? 3 : 2;
-      RSN_CUDA(c, cudaMemcpyAsync(rn.data(), q.rn.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-      RSN_CUDA(c, cudaMemcpyAsync(tt.data(), q.tt.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-      int hstat[4] = {0, 0, 0, 0};
-      RSN_CUDA(c, cudaMemcpyAsync(hstat, q.stat.p, sizeof(hstat), cudaMemcpyDeviceToHost, c->st));
-      RSN_CUDA(c, cudaStreamSynchronize(c->st));
-      if (hstat[2]) RSN_FAIL(c, RSN_ETIMEOUT, "an operator kernel gave up waiting for a bulk copy");
-      std::vector<int> keep;
-      for (int k : act) {
-        bool all = true, progress = false;
+    const int nbe = (n_cols + B - 1) / B;  // blocks per energy
+    const long long nb = (long long)n_e * nbe;
+    std::vector<double> t_host((size_t)std::max(1, n_e) * std::max(1, n_cols), 0.0);
+    rsn_status worst = RSN_OK;
+    long long n_fail = 0, n_brk = 0, n_late = 0, n_hand = 0;
+    const size_t per_member = (size_t)N * (4 * sizeof(float2) + 2 * sizeof(double2)) + 4096;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    // members per wave: within memory and within a launch's grid.y (one CTA row per member)
+    const long long cap = std::max<long long>(
+        1, std::min<long long>(kMaxApplyRhs / B, (long long)(0.5 * (double)fr / ((double)per_member * B))));
+    for (long long b0 = 0; b0 < nb; b0 += cap) {
+      BlkRun br;
+      br.B = B;
+      br.nbw = (int)std::min<long long>(cap, nb - b0);
+      br.S = br.nbw * B;
+      const int nbw = br.nbw, S = br.S;
+      // members: E, column, real (output index) or padding (-1)
+      std::vector<double> memE(S);
+      std::vector<int> memCol(S);
+      std::vector<long long> memOut(S);
+      for (int k = 0; k < nbw; ++k) {
+        const long long gb = b0 + k;
+        const int e = (int)(gb / nbe), cb = (int)(gb % nbe);
+        int np = 0;
         for (int a = 0; a < B; ++a) {
+          const int kc = cb * B + a;
           const int v = k * B + a;
-          if (memOut[v] < 0) continue;
-          bool ok = std::isfinite(rn[v]) && rn[v] <= o->tol;
-          if (ok && o->tol_T > 0.0) {
-            if (outer < 2) {
-              ok = false;
-            } else {
-              const double dt = std::fabs(tt[v] - t_prev[v]);
-              const double red = std::min(1.0, 10.0 * rn[v] / std::max(rn_prev[v], 1e-300));
-              ok = dt * red <= o->tol_T * tt[v] || dt == 0.0;
-            }
+          memE[v] = E[e];
+          if (kc < n_cols) {
+            memCol[v] = cols[kc];
+            memOut[v] = (long long)e * n_cols + kc;
+          } else {
+            memCol[v] = pad[np++];
+            memOut[v] = -1;
           }
-          if (!ok) all = false;
-          // progress: the residual halved, or (at the residual target) the T
-          // partial's change halved
-          const double dt = std::fabs(tt[v] - t_prev[v]);
-          if (outer == 0 || rn[v] < 0.5 * rn_prev[v] || (rn[v] <= o->tol && dt < 0.5 * dt_prev[v])) progress = true;
         }
+      }
+      // buffers
+      const size_t vb32 = (size_t)S * N * sizeof(float2), vb64 = (size_t)S * N * sizeof(double2);
+      RSN_CUDA(c, q.W.ensure(vb32));
+      RSN_CUDA(c, q.P.ensure(vb32));
+      RSN_CUDA(c, q.AP.ensure(vb32));
+      RSN_CUDA(c, q.D.ensure(vb32));
+      RSN_CUDA(c, q.X.ensure(vb64));
+      RSN_CUDA(c, q.R.ensure(vb64));
+      int nchunk = std::max(1, std::min(64, (4 * 152 + nbw - 1) / nbw));
+      long long chunk_pts = (N + nchunk - 1) / nchunk;
+      chunk_pts = (chunk_pts + kBlkTile - 1) / kBlkTile * kBlkTile;
+      nchunk = (int)((N + chunk_pts - 1) / chunk_pts);
+      int nchunkR = std::max(1, std::min(32, (8 * 152 + S - 1) / S));
+      long long chunkR_pts = (N + nchunkR - 1) / nchunkR;
+      nchunkR = (int)((N + chunkR_pts - 1) / chunkR_pts);
+      const size_t bb2 = (size_t)nbw * B * B;
+      RSN_CUDA(c, q.part.ensure((size_t)nbw * nchunk * 2 * B * B * sizeof(double2)));
+      RSN_CUDA(c, q.xi.ensure(bb2 * sizeof(double2)));
+      RSN_CUDA(c, q.QQ.ensure(bb2 * sizeof(double2)));
+      RSN_CUDA(c, q.xi0n.ensure((size_t)S * sizeof(double)));
+      RSN_CUDA(c, q.alpha.ensure(bb2 * sizeof(float2)));
+      RSN_CUDA(c, q.axi.ensure(bb2 * sizeof(float2)));
+      RSN_CUDA(c, q.tinv.ensure(bb2 * sizeof(float2)));
+      RSN_CUDA(c, q.tinv64.ensure(bb2 * sizeof(double2)));
+      RSN_CUDA(c, q.beta.ensure(bb2 * sizeof(float2)));
+      RSN_CUDA(c, q.flag.ensure((size_t)nbw * sizeof(int)));
+      RSN_CUDA(c, q.its.ensure((size_t)nbw * sizeof(int)));
+      RSN_CUDA(c, q.rpart.ensure((size_t)S * nchunkR * 2 * sizeof(double)));
+      RSN_CUDA(c, q.rn.ensure((size_t)S * sizeof(double)));
+      RSN_CUDA(c, q.tt.ensure((size_t)S * sizeof(double)));
+      RSN_CUDA(c, q.blist.ensure((size_t)nbw * sizeof(int)));
+      RSN_CUDA(c, q.col.ensure((size_t)S * sizeof(int)));
+      RSN_CUDA(c, q.vE.ensure((size_t)S * sizeof(double)));
+      RSN_CUDA(c, q.vjunc.ensure((size_t)S * sizeof(int)));
+      RSN_CUDA(c, q.voff.ensure((size_t)S * sizeof(long long)));
+      RSN_CUDA(c, q.cbuf.ensure((size_t)S * std::max(1, c->n_proj) * sizeof(double2)));
+      RSN_CUDA(c, q.dev.ensure(sizeof(BlkDev)));
+      RSN_CUDA(c, q.bdev.ensure(sizeof(BatchDev)));
+      RSN_CUDA(c, q.jd.ensure(2 * sizeof(JuncDev)));
+      RSN_CUDA(c, q.stat.ensure(4 * sizeof(int)));
+      RSN_CUDA(c, cudaMemsetAsync(q.stat.p, 0, 4 * sizeof(int), c->st));
+      RSN_CUDA(c, cudaMemsetAsync(q.vjunc.p, 0, (size_t)S * sizeof(int), c->st));
+      RSN_CUDA(c, cudaMemsetAsync(q.X.p, 0, vb64, c->st));
+      RSN_CUDA(c, cudaMemsetAsync(q.flag.p, 0, (size_t)nbw * sizeof(int), c->st));
+      RSN_CUDA(c, cudaMemcpyAsync(q.col.p, memCol.data(), (size_t)S * sizeof(int), cudaMemcpyHostToDevice, c->st));
+      BlkDev hd;
+      memset(&hd, 0, sizeof(hd));
+      hd.B = B;
+      hd.N = N;
+      hd.nchunk = nchunk;
+      hd.chunk_pts = chunk_pts;
+      hd.nchunkR = nchunkR;
+      hd.chunkR_pts = chunkR_pts;
+      RSN_CUDA(c, q.icap.ensure((size_t)nbw * sizeof(int)));
+      hd.icap = q.icap.as<int>();
+      hd.tol_in = tol_in;
+      hd.blist = q.blist.as<int>();
+      hd.col = q.col.as<int>();
+      hd.gl = c->gld.as<double>();
+      hd.xi = q.xi.as<double2>();
+      hd.QQ = q.QQ.as<double2>();
+      hd.xi0n = q.xi0n.as<double>();
+      hd.part = q.part.as<double2>();
+      hd.alpha = q.alpha.as<float2>();
+      hd.axi = q.axi.as<float2>();
+      hd.tinv = q.tinv.as<float2>();
+      hd.tinv64 = q.tinv64.as<double2>();
+      hd.beta = q.beta.as<float2>();
+      hd.flag = q.flag.as<int>();
+      hd.its = q.its.as<int>();
+      hd.W = q.W.as<float2>();
+      hd.P = q.P.as<float2>();
+      hd.AP = q.AP.as<float2>();
+      hd.D = q.D.as<float2>();
+      hd.X = q.X.as<double2>();
+      hd.R = q.R.as<double2>();
+      hd.rpart = q.rpart.as<double>();
+      hd.rn = q.rn.as<double>();
+      hd.tt = q.tt.as<double>();
+      RSN_CUDA(c, cudaMemcpyAsync(q.dev.p, &hd, sizeof(hd), cudaMemcpyHostToDevice, c->st));
+      const BlkDev* dd = q.dev.as<BlkDev>();
+      // operator tilings: FP32 apply of P, FP64 apply of X
+      const bool al32 = (N * (long long)sizeof(float2)) % 16 == 0;
+      const Tiling t32 = choose_tiling(c, false, OP_APPLY, S, al32);
+      const Tiling t64 = choose_tiling(c, true, OP_APPLY, S, false);
+      {
+        JuncDev js[2] = {c->jh, c->jh};
+        const Tiling* tt2[2] = {&t32, &t64};
+        for (int k = 0; k < 2; ++k) {
+          const Tiling& t = *tt2[k];
+          js[k].TY = t.TY;
+          js[k].Lz = t.Lz;
+          js[k].ytiles = t.ytiles;
+          js[k].ztiles = t.ztiles;
+          js[k].nA = t.n;
+          js[k].nR = t.n;
+          js[k].kind = t.plane ? kOpPlane : t.pair ? kOpPair : t.tma ? kOpTma : kOpReg;
+        }
+        RSN_CUDA(c, cudaMemcpyAsync(q.jd.p, js, 2 * sizeof(JuncDev), cudaMemcpyHostToDevice, c->st));
+      }
+      const JuncDev* j32 = q.jd.as<JuncDev>();
+      const JuncDev* j64 = q.jd.as<JuncDev>() + 1;
+      // outer loop
+      std::vector<int> act(nbw);
+      for (int k = 0; k < nbw; ++k) act[k] = k;
+      std::vector<double> rn(S), tt(S), rn_prev(S, 1.0), t_prev(S, 0.0), dt_prev(S, HUGE_VAL);
+      std::vector<long long> apps(nbw, 0);
+      std::vector<int> stall(nbw, 0), failed(nbw, 0), flags(nbw), its(nbw);
+      // Inner iteration cap per block: the first inner solve (from the unit
+      // columns) may take up to min(max_iter, kBlkInnerCap); a restart that runs
+      // past twice the first solve's count has lost its block's orthogonality
+      // (FP32 Gram matrices of nearly dependent residual directions) and is
+      // abandoned, the block going to the plain solver.
+      std::vector<int> icap(nbw, std::min(o->max_iter, kBlkInnerCap));
+      for (int outer = 0;; ++outer) {
+        if (o->deadline_ms > 0) {
+          const double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+          if (el > o->deadline_ms) {
+            for (int k : act) failed[k] = 2;
+            break;
+          }
+        }
+        if (outer > 0) {
+          // an inner solve that hit its cap or broke down leaves a correction of
+          // unknown quality: its block keeps its last FP64 iterate and goes to the
+          // plain solver
+          std::vector<int> good;
+          for (int k : act)
+            if (flags[k] == 1) good.push_back(k);
+            else failed[k] = 1;
+          act.swap(good);
+          if (act.empty()) break;
+        }
+        const int na = (int)act.size();
+        if ((rs = blk_set_lists(c, br, act, memE)) != RSN_OK) return rs;
+        if (outer > 0) {
+          RSN_CUDA(c, launch_blk_xupd(B, na, c->st, dd, N));
+          if ((rs = blk_apply(c, t64, j64, false, na * B, q.X.p, q.R.p)) != RSN_OK) return rs;
+          for (int k : act) apps[k] += 1;
+        }
+        RSN_CUDA(c, launch_blk_resid(B, na, nchunkR, outer > 0, c->st, dd));
+        RSN_CUDA(c, launch_blk_norm(B, na, nchunkR, c->st, dd));
+        c->st_launches += outer > 0 ? 3 : 2;
+        RSN_CUDA(c, cudaMemcpyAsync(rn.data(), q.rn.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        RSN_CUDA(c, cudaMemcpyAsync(tt.data(), q.tt.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        int hstat[4] = {0, 0, 0, 0};
+        RSN_CUDA(c, cudaMemcpyAsync(hstat, q.stat.p, sizeof(hstat), cudaMemcpyDeviceToHost, c->st));
+        RSN_CUDA(c, cudaStreamSynchronize(c->st));
+        if (hstat[2]) RSN_FAIL(c, RSN_ETIMEOUT, "an operator kernel gave up waiting for a bulk copy");
+        std::vector<int> keep;
+        for (int k : act) {
+          bool all = true, progress = false;
+          for (int a = 0; a < B; ++a) {
+            const int v = k * B + a;
+            if (memOut[v] < 0) continue;
+            bool ok = std::isfinite(rn[v]) && rn[v] <= o->tol;
+            if (ok && o->tol_T > 0.0) {
+              if (outer < 2) {
+                ok = false;
+              } else {
+                const double dt = std::fabs(tt[v] - t_prev[v]);
+                const double red = std::min(1.0, 10.0 * rn[v] / std::max(rn_prev[v], 1e-300));
+                ok = dt * red <= o->tol_T * tt[v] || dt == 0.0;
+              }
+            }
+            if (!ok) all = false;
+            // progress: the residual halved, or (at the residual target) the T
+            // partial's change halved
+            const double dt = std::fabs(tt[v] - t_prev[v]);
+            if (outer == 0 || rn[v] < 0.5 * rn_prev[v] || (rn[v] <= o->tol && dt < 0.5 * dt_prev[v])) progress = true;
+          }
+          for (int a = 0; a < B; ++a) {
+            const int v = k * B + a;
+            if (outer > 0) dt_prev[v] = std::fabs(tt[v] - t_prev[v]);
+            rn_prev[v] = rn[v];
+            t_prev[v] = tt[v];
+          }
+          if (all) continue;
+          stall[k] = progress ? 0 : stall[k] + 1;
+          if (stall[k] >= 3 || outer >= o->max_outer) {
+            failed[k] = 1;
+            continue;
+          }
+          keep.push_back(k);
+        }
+        act.swap(keep);
+        if (act.empty()) break;
+        // inner solve on the normalised residual block
+        const int na2 = (int)act.size();
+        if ((rs = blk_set_lists(c, br, act, memE)) != RSN_OK) return rs;
+        // the previous inner solve left its end state in the flags; the kernels
+        // of the new one (the Gram of W_0 first) run only on unflagged blocks
+        RSN_CUDA(c, cudaMemsetAsync(q.flag.p, 0, (size_t)nbw * sizeof(int), c->st));
+        RSN_CUDA(c, cudaMemcpyAsync(q.icap.p, icap.data(), (size_t)nbw * sizeof(int), cudaMemcpyHostToDevice, c->st));
+        RSN_CUDA(c, launch_blk_scale(B, na2, c->st, dd, N));
+        RSN_CUDA(c, launch_blk_gram64(B, na2, nchunk, c->st, dd));
+        RSN_CUDA(c, launch_blk_small(B, 0, na2, c->st, dd));
+        RSN_CUDA(c, launch_blk_q0(B, na2, c->st, dd, N));
+        c->st_launches += 4;
+        std::vector<int> in = act;
+        const int kChunk = 8;
+        while (!in.empty()) {
+          const int ni = (int)in.size();
+          for (int it = 0; it < kChunk; ++it) {
+            RSN_CUDA(c, launch_blk_comb_p(B, ni, c->st, dd, N));
+            if ((rs = blk_apply(c, t32, j32, true, ni * B, q.P.p, q.AP.p)) != RSN_OK) return rs;
+            RSN_CUDA(c, launch_blk_gram(B, 0, ni, nchunk, c->st, dd));
+            RSN_CUDA(c, launch_blk_small(B, 1, ni, c->st, dd));
+            RSN_CUDA(c, launch_blk_comb_w(B, ni, c->st, dd, N));
+            RSN_CUDA(c, launch_blk_gram(B, 1, ni, nchunk, c->st, dd));
+            RSN_CUDA(c, launch_blk_small(B, 2, ni, c->st, dd));
+            c->st_launches += 6;
+          }
+          RSN_CUDA(c, cudaMemcpyAsync(flags.data(), q.flag.p, (size_t)nbw * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+          RSN_CUDA(c, cudaStreamSynchronize(c->st));
+          std::vector<int> nxt;
+          for (int k : in)
+            if (flags[k] == 0) nxt.push_back(k);
+          if (nxt.size() != in.size()) {
+            in.swap(nxt);
+            if (!in.empty() && (rs = blk_set_lists(c, br, in, memE)) != RSN_OK) return rs;
+          }
+        }
+        RSN_CUDA(c, cudaMemcpyAsync(its.data(), q.its.p, (size_t)nbw * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        RSN_CUDA(c, cudaStreamSynchronize(c->st));
+        for (int k : act) {
+          apps[k] += its[k];
+          if (flags[k] == 2) ++n_brk;
+          if (outer == 0) icap[k] = std::min(icap[k], std::max(64, 2 * its[k]));
+        }
+      }
+      // Blocks that did not finish: their columns go to the plain slot-pool
+      // solver (FP32 recurrence with FP64 reliable updates and its own FP64
+      // re-solve of stalled systems), warm-started from the block's last FP64
+      // iterate.
+      std::vector<int> hv;
+      for (int k = 0; k < nbw; ++k)
+        if (failed[k] == 1)
+          for (int a = 0; a < B; ++a)
+            if (memOut[k * B + a] >= 0) hv.push_back(k * B + a);
+      std::vector<int> hst(S, 0), hit(S, 0);
+      if (!hv.empty()) {
+        const int nh = (int)hv.size();
+        StreamIn in;
+        in.resize(nh);
+        for (int u = 0; u < nh; ++u) {
+          in.E[u] = memE[hv[u]];
+          in.col[u] = memCol[hv[u]];
+          in.xo[u] = (long long)hv[u] * N;
+          in.bn2[u] = 1.0;  // ||e_col||^2: start from the iterate in X
+        }
+        StreamOut so;
+        if ((rs = run_stream(c, o, in, q.X.as<double2>(), nullptr, true, 0, t_start, so)) != RSN_OK) return rs;
+        std::vector<double> th(nh);
+        RSN_CUDA(c, cudaMemcpyAsync(th.data(), c->cb.out_t.p, nh * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        RSN_CUDA(c, cudaStreamSynchronize(c->st));
+        std::vector<int> F;
+        StreamIn sub;
+        for (int u = 0; u < nh; ++u) {
+          const int v = hv[u];
+          tt[v] = th[u];
+          rn[v] = so.relres[u];
+          hit[v] = so.iters[u];
+          hst[v] = so.status[u];
+          if (so.status[u] != 0 && o->precision == RSN_MIXED) {
+            F.push_back(u);
+            sub.push(in, (size_t)u);
+            sub.bn2.back() = 0.0;  // cold start: a stalled FP32 iterate slows FP64 COCG down
+          }
+        }
+        if (!F.empty()) {
+          rsn_solver_opts o64;
+          rsn_default_opts(RSN_FP64, &o64);
+          o64.tol = o->tol;
+          o64.tol_T = o->tol_T;
+          o64.deadline_ms = o->deadline_ms;
+          StreamOut s2;
+          if ((rs = run_stream(c, &o64, sub, q.X.as<double2>(), nullptr, true, 0, t_start, s2)) != RSN_OK) return rs;
+          std::vector<double> t2(F.size());
+          RSN_CUDA(c, cudaMemcpyAsync(t2.data(), c->cb.out_t.p, F.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                      c->st));
+          RSN_CUDA(c, cudaStreamSynchronize(c->st));
+          for (size_t f = 0; f < F.size(); ++f) {
+            const int v = hv[F[f]];
+            tt[v] = t2[f];
+            rn[v] = s2.relres[f];
+            hit[v] += s2.iters[f];
+            hst[v] = s2.status[f];
+          }
+        }
+        n_hand += nh;
+      }
+      // outputs of the real members
+      for (int k = 0; k < nbw; ++k) {
+        if (failed[k] == 2) ++n_late;
         for (int a = 0; a < B; ++a) {
           const int v = k * B + a;
-          if (outer > 0) dt_prev[v] = std::fabs(tt[v] - t_prev[v]);
-          rn_prev[v] = rn[v];
-          t_prev[v] = tt[v];
+          const long long out = memOut[v];
+          if (out < 0) continue;
+          t_host[out] = tt[v];
+          if (t_out) t_out[out] = tt[v];
+          const bool bad = failed[k] == 2 || (failed[k] == 1 && hst[v] != 0);
+          if (bad && failed[k] == 1) ++n_fail;
+          if (iters) iters[out] = bad ? -1 : (int32_t)std::min<long long>(apps[k] + hit[v], INT32_MAX);
+          if (relres) relres[out] = rn[v];
+          c->st_iters += apps[k];
+          if (x_out)
+            RSN_CUDA(c, cudaMemcpyAsync(x_out + out * N, q.X.as<double2>() + (size_t)v * N, N * sizeof(double2),
+                                        cudaMemcpyDeviceToDevice, c->st));
         }
-        if (all) continue;
-        stall[k] = progress ? 0 : stall[k] + 1;
-        if (stall[k] >= 3 || outer >= o->max_outer) {
-          failed[k] = 1;
-          continue;
-        }
-        keep.push_back(k);
-      }
-      act.swap(keep);
-      if (act.empty()) break;
-      // inner solve on the normalised residual block
-      const int na2 = (int)act.size();
-      if ((rs = blk_set_lists(c, br, act, memE)) != RSN_OK) return rs;
-      // the previous inner solve left its end state in the flags; the kernels
-      // of the new one (the Gram of W_0 first) run only on unflagged blocks
-      RSN_CUDA(c, cudaMemsetAsync(q.flag.p, 0, (size_t)nbw * sizeof(int), c->st));
-      RSN_CUDA(c, cudaMemcpyAsync(q.icap.p, icap.data(), (size_t)nbw * sizeof(int), cudaMemcpyHostToDevice, c->st));
-      RSN_CUDA(c, launch_blk_scale(B, na2, c->st, dd, N));
-      RSN_CUDA(c, launch_blk_gram64(B, na2, nchunk, c->st, dd));
-      RSN_CUDA(c, launch_blk_small(B, 0, na2, c->st, dd));
-      RSN_CUDA(c, launch_blk_q0(B, na2, c->st, dd, N));
-      c->st_launches += 4;
-      std::vector<int> in = act;
-      const int kChunk = 8;
-      while (!in.empty()) {
-        const int ni = (int)in.size();
-        for (int it = 0; it < kChunk; ++it) {
-          RSN_CUDA(c, launch_blk_comb_p(B, ni, c->st, dd, N));
-          if ((rs = blk_apply(c, t32, j32, true, ni * B, q.P.p, q.AP.p)) != RSN_OK) return rs;
-          RSN_CUDA(c, launch_blk_gram(B, 0, ni, nchunk, c->st, dd));
-          RSN_CUDA(c, launch_blk_small(B, 1, ni, c->st, dd));
-          RSN_CUDA(c, launch_blk_comb_w(B, ni, c->st, dd, N));
-          RSN_CUDA(c, launch_blk_gram(B, 1, ni, nchunk, c->st, dd));
-          RSN_CUDA(c, launch_blk_small(B, 2, ni, c->st, dd));
-          c->st_launches += 6;
-        }
-        RSN_CUDA(c, cudaMemcpyAsync(flags.data(), q.flag.p, (size_t)nbw * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-        RSN_CUDA(c, cudaStreamSynchronize(c->st));
-        std::vector<int> nxt;
-        for (int k : in)
-          if (flags[k] == 0) nxt.push_back(k);
-        if (nxt.size() != in.size()) {
-          in.swap(nxt);
-          if (!in.empty() && (rs = blk_set_lists(c, br, in, memE)) != RSN_OK) return rs;
-        }
-      }
-      RSN_CUDA(c, cudaMemcpyAsync(its.data(), q.its.p, (size_t)nbw * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-      RSN_CUDA(c, cudaStreamSynchronize(c->st));
-      for (int k : act) {
-        apps[k] += its[k];
-        if (flags[k] == 2) ++n_brk;
-        if (outer == 0) icap[k] = std::min(icap[k], std::max(64, 2 * its[k]));
       }
     }
-    // Blocks that did not finish: their columns go to the plain slot-pool
-    // solver (FP32 recurrence with FP64 reliable updates and its own FP64
-    // re-solve of stalled systems), warm-started from the block's last FP64
-    // iterate.
-    std::vector<int> hv;
-    for (int k = 0; k < nbw; ++k)
-      if (failed[k] == 1)
-        for (int a = 0; a < B; ++a)
-          if (memOut[k * B + a] >= 0) hv.push_back(k * B + a);
-    std::vector<int> hst(S, 0), hit(S, 0);
-    if (!hv.empty()) {
-      const int nh = (int)hv.size();
-      StreamIn in;
-      in.resize(nh);
-      for (int u = 0; u < nh; ++u) {
-        in.E[u] = memE[hv[u]];
-        in.col[u] = memCol[hv[u]];
-        in.xo[u] = (long long)hv[u] * N;
-        in.bn2[u] = 1.0;  // ||e_col||^2: start from the iterate in X
+    if (n_fail > 0) worst = RSN_ENOCONV;
+    if (n_late > 0) worst = RSN_ETIMEOUT;
+    if (T && n_e > 0) {
+      RSN_CUDA(c, q.t_all.ensure(t_host.size() * sizeof(double)));
+      RSN_CUDA(c, q.gr_cols.ensure(std::max(1, n_cols) * sizeof(double)));
+      RSN_CUDA(c, q.Td.ensure(n_e * sizeof(double)));
+      std::vector<double> hgr(std::max(1, n_cols));
+      for (int k = 0; k < n_cols; ++k) hgr[k] = c->gr[cols[k]];
+      RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, t_host.data(), t_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      RSN_CUDA(c, cudaMemcpyAsync(q.gr_cols.p, hgr.data(), hgr.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      if (n_cols > 0) {
+        RSN_CUDA(c, launch_t_final(n_e, n_cols, c->st, q.t_all.as<double>(), q.gr_cols.as<double>(), q.Td.as<double>()));
+        c->st_launches += 1;
+      } else {
+        RSN_CUDA(c, cudaMemsetAsync(q.Td.p, 0, n_e * sizeof(double), c->st));
       }
-      StreamOut so;
-      if ((rs = run_stream(c, o, in, q.X.as<double2>(), nullptr, true, 0, t_start, so)) != RSN_OK) return rs;
-      std::vector<double> th(nh);
-      RSN_CUDA(c, cudaMemcpyAsync(th.data(), c->cb.out_t.p, nh * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-      RSN_CUDA(c, cudaStreamSynchronize(c->st));
-      std::vector<int> F;
-      StreamIn sub;
-      for (int u = 0; u < nh; ++u) {
-        const int v = hv[u];
-        tt[v] = th[u];
-        rn[v] = so.relres[u];
-        hit[v] = so.iters[u];
-        hst[v] = so.status[u];
-        if (so.status[u] != 0 && o->precision == RSN_MIXED) {
-          F.push_back(u);
-          sub.push(in, (size_t)u);
-          sub.bn2.back() = 0.0;  // cold start: a stalled FP32 iterate slows FP64 COCG down
-        }
-      }
-      if (!F.empty()) {
-        rsn_solver_opts o64;
-        rsn_default_opts(RSN_FP64, &o64);
-        o64.tol = o->tol;
-        o64.tol_T = o->tol_T;
-        o64.deadline_ms = o->deadline_ms;
-        StreamOut s2;
-        if ((rs = run_stream(c, &o64, sub, q.X.as<double2>(), nullptr, true, 0, t_start, s2)) != RSN_OK) return rs;
-        std::vector<double> t2(F.size());
-        RSN_CUDA(c, cudaMemcpyAsync(t2.data(), c->cb.out_t.p, F.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                    c->st));
-        RSN_CUDA(c, cudaStreamSynchronize(c->st));
-        for (size_t f = 0; f < F.size(); ++f) {
-          const int v = hv[F[f]];
-          tt[v] = t2[f];
-          rn[v] = s2.relres[f];
-          hit[v] += s2.iters[f];
-          hst[v] = s2.status[f];
-        }
-      }
-      n_hand += nh;
+      RSN_CUDA(c, cudaMemcpyAsync(T, q.Td.p, n_e * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     }
-    // outputs of the real members
-    for (int k = 0; k < nbw; ++k) {
-      if (failed[k] == 2) ++n_late;
-      for (int a = 0; a < B; ++a) {
-        const int v = k * B + a;
-        const long long out = memOut[v];
-        if (out < 0) continue;
-        t_host[out] = tt[v];
-        if (t_out) t_out[out] = tt[v];
-        const bool bad = failed[k] == 2 || (failed[k] == 1 && hst[v] != 0);
-        if (bad && failed[k] == 1) ++n_fail;
-        if (iters) iters[out] = bad ? -1 : (int32_t)std::min<long long>(apps[k] + hit[v], INT32_MAX);
-        if (relres) relres[out] = rn[v];
-        c->st_iters += apps[k];
-        if (x_out)
-          RSN_CUDA(c, cudaMemcpyAsync(x_out + out * N, q.X.as<double2>() + (size_t)v * N, N * sizeof(double2),
-                                      cudaMemcpyDeviceToDevice, c->st));
-      }
-    }
-  }
-  if (n_fail > 0) worst = RSN_ENOCONV;
-  if (n_late > 0) worst = RSN_ETIMEOUT;
-  if (T && n_e > 0) {
-    RSN_CUDA(c, q.t_all.ensure(t_host.size() * sizeof(double)));
-    RSN_CUDA(c, q.gr_cols.ensure(std::max(1, n_cols) * sizeof(double)));
-    RSN_CUDA(c, q.Td.ensure(n_e * sizeof(double)));
-    std::vector<double> hgr(std::max(1, n_cols));
-    for (int k = 0; k < n_cols; ++k) hgr[k] = c->gr[cols[k]];
-    RSN_CUDA(c, cudaMemcpyAsync(q.t_all.p, t_host.data(), t_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    RSN_CUDA(c, cudaMemcpyAsync(q.gr_cols.p, hgr.data(), hgr.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    if (n_cols > 0) {
-      RSN_CUDA(c, launch_t_final(n_e, n_cols, c->st, q.t_all.as<double>(), q.gr_cols.as<double>(), q.Td.as<double>()));
-      c->st_launches += 1;
-    } else {
-      RSN_CUDA(c, cudaMemsetAsync(q.Td.p, 0, n_e * sizeof(double), c->st));
-    }
-    RSN_CUDA(c, cudaMemcpyAsync(T, q.Td.p, n_e * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-  }
-  RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
-  RSN_CUDA(c, cudaStreamSynchronize(c->st));
-  float ms = 0;
-  cudaEventElapsedTime(&ms, c->t0, c->t1);
-  c->st_ms = ms;
-  c->st_fallback = n_hand;
-  (void)n_brk;
-  if (worst != RSN_OK)
-    RSN_FAIL(c, worst, "%lld columns did not reach tol / tol_T, %lld blocks stopped at the deadline", n_fail, n_late);
-  return RSN_OK;
+    RSN_CUDA(c, cudaEventRecord(c->t1, c->st));
+    RSN_CUDA(c, cudaStreamSynchronize(c->st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->t0, c->t1);
+    c->st_ms = ms;
+    c->st_fallback = n_hand;
+    (void)n_brk;
+    if (worst != RSN_OK)
+      RSN_FAIL(c, worst, "%lld columns did not reach tol / tol_T, %lld blocks stopped at the deadline", n_fail, n_late);
+    return RSN_OK;
   };
   rs = run();
   const rsn_status rl = leave(c);
